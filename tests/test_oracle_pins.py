@@ -1,0 +1,305 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+of the Chebyshev polynomials, numpy's independent Chebyshev routines,
+brute-force sums on tiny tensors, the aliasing identity at Lobatto nodes,
+spectral decay on analytic functions, and (for the game) the closed-form
+linear-quadratic recursion plus a brute-force Bellman check of its fixed point.
+"""
+import math
+
+import numpy as np
+import numpy.polynomial.chebyshev as npc
+import pytest
+
+import oracle as O
+from paper_2307_04688_gb300 import inputs as I
+
+
+def lobatto(n):
+    N = n - 1
+    return np.cos(np.pi * np.arange(n) / N)
+
+
+# ---- Section 3.1: T_n, nodes --------------------------------------------------
+
+def test_nodes_are_cos_pi_k_over_N_and_extrema_of_T_N():
+    for n in (2, 3, 9, 17, 33, 64):
+        a = O.nodes(n)
+        N = n - 1
+        assert np.allclose(a, np.cos(np.pi * np.arange(n) / N), atol=0, rtol=0)
+        T = np.array([O.cheb_T(n, x)[N] for x in a])
+        assert np.allclose(T, (-1.0) ** np.arange(n), atol=1e-12)
+
+
+def test_T_closed_form_on_and_off_the_interval():
+    rng = np.random.default_rng(1)
+    for theta in rng.uniform(0, np.pi, 20):
+        T = O.cheb_T(65, math.cos(theta))
+        assert np.allclose(T, np.cos(np.arange(65) * theta), atol=2e-13)
+    for x in (1.01, 1.3, -1.2):
+        T = O.cheb_T(20, x)
+        k = np.arange(20)
+        ref = np.sign(x) ** k * np.cosh(k * np.arccosh(abs(x)))
+        assert np.allclose(T, ref, rtol=1e-12)
+
+
+# ---- Section 3.1: one-dimensional fit -----------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 5, 9, 17, 33, 64])
+def test_fit_1d_reproduces_polynomials_and_matches_c1v(n):
+    rng = np.random.default_rng(n)
+    c = rng.standard_normal(n)
+    F = npc.chebval(lobatto(n), c)          # numpy's evaluation at the nodes
+    assert np.abs(O.fit_1d(F) - c).max() < 1e-13 * max(1.0, np.abs(c).max()) * n
+    assert np.abs(O.c1v(F) - c).max() < 1e-13 * max(1.0, np.abs(c).max()) * n
+
+
+def test_fit_1d_equals_numpy_interpolation_at_lobatto_nodes():
+    rng = np.random.default_rng(7)
+    for n in (4, 9, 17):
+        F = rng.standard_normal(n)          # arbitrary data, not a polynomial of low degree
+        ref = npc.chebfit(lobatto(n), F, n - 1)
+        assert np.allclose(O.fit_1d(F), ref, atol=1e-11)
+        assert np.allclose(O.c1v(F), O.fit_1d(F), atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [5, 9, 17])
+def test_fit_aliasing_closed_form(n):
+    """T_j at the Lobatto nodes equals T_alias(j), alias(j) = j mod 2N folded into [0, N]."""
+    N = n - 1
+    x = lobatto(n)
+    for j in range(N + 1, 4 * N + 1):
+        F = np.cos(j * np.arccos(np.clip(x, -1, 1)))
+        t = j % (2 * N)
+        alias = t if t <= N else 2 * N - t
+        e = np.zeros(n)
+        e[alias] = 1.0
+        assert np.abs(O.fit_1d(F) - e).max() < 1e-13, (j, alias)
+
+
+def test_spectral_decay_on_analytic_function():
+    """|f - I_N f| ~ C rho^-N for f = 1/(2 - x), analytic inside the Bernstein ellipse rho = 2 + sqrt 3."""
+    xs = np.linspace(-1, 1, 2001)
+    f = lambda x: 1.0 / (2.0 - x)
+    Ns, errs = [], []
+    for N in range(4, 25, 2):
+        n = N + 1
+        p = O.fit_1d(f(lobatto(n)))
+        err = np.abs(npc.chebval(xs, p) - f(xs)).max()
+        Ns.append(N)
+        errs.append(err)
+    slope = np.polyfit(Ns, np.log(errs), 1)[0]
+    assert abs(slope + math.log(2 + math.sqrt(3))) < 0.1 * math.log(2 + math.sqrt(3))
+    # two-dimensional product of two such functions, through fit_nd / eval_grid
+    n = 17
+    a = lobatto(n)
+    G = np.outer(f(a), f(0.5 * a))
+    c = O.fit_nd(G)
+    g = np.linspace(-1, 1, 41)
+    D = O.eval_grid(c, [g, g])
+    assert np.abs(D - np.outer(f(g), f(0.5 * g))).max() < 5e-8
+
+
+# ---- Section 3.1: derivative (Proposition 3.1) -------------------------------
+
+def test_derivative_coefficients():
+    rng = np.random.default_rng(3)
+    for n in (2, 3, 8, 17):
+        p = rng.standard_normal(n)
+        q = O.deriv_coeffs(p)
+        ref = npc.chebder(p) if n > 1 else np.zeros(0)
+        assert np.allclose(q[: n - 1], ref, atol=1e-12)
+        assert q[n - 1] == 0.0
+    # closed form T_k'(cos t) = k sin(k t) / sin(t)
+    for k in range(1, 12):
+        e = np.zeros(12)
+        e[k] = 1.0
+        q = O.deriv_coeffs(e)
+        for t in (0.3, 1.1, 2.5):
+            assert abs(O.series(q, math.cos(t)) - k * math.sin(k * t) / math.sin(t)) < 1e-11
+
+
+# ---- Sections 3.1-3.3: n-dimensional fit and evaluation -----------------------
+
+@pytest.mark.parametrize("shape", [(3,), (5, 4), (3, 4, 5), (2, 3, 2, 3)])
+def test_fit_nd_and_cnv_reproduce_tensor_polynomials(shape):
+    rng = np.random.default_rng(len(shape))
+    c = rng.standard_normal(shape)
+    # nodal values by brute-force direct summation over every multi-index
+    G = np.zeros(shape)
+    for idx in np.ndindex(*shape):
+        x = [lobatto(shape[s])[idx[s]] for s in range(len(shape))]
+        tot = 0.0
+        for l in np.ndindex(*shape):
+            t = c[l]
+            for s in range(len(shape)):
+                t *= math.cos(l[s] * math.acos(max(-1.0, min(1.0, x[s]))))
+            tot += t
+        G[idx] = tot
+    assert np.abs(O.fit_nd(G) - c).max() < 1e-13
+    assert np.abs(O.cnv(G) - c).max() < 1e-13
+
+
+def test_eval_matches_numpy_and_brute_force():
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal((4, 5, 3))
+    xs = [rng.uniform(-1, 1, 6), rng.uniform(-1, 1, 7), rng.uniform(-1, 1, 5)]
+    D = O.eval_grid(c, xs)
+    assert np.allclose(D, npc.chebgrid3d(xs[0], xs[1], xs[2], c), atol=1e-13)
+    P = rng.uniform(-1, 1, (50, 3))
+    v = O.eval_points(c, P)
+    assert np.allclose(v, npc.chebval3d(P[:, 0], P[:, 1], P[:, 2], c), atol=1e-13)
+    for j in range(5):
+        assert abs(O.eval_direct(c, P[j]) - v[j]) < 1e-14
+        assert abs(O.eval_nested(c, P[j]) - v[j]) < 1e-13
+    # a physical box [a, b] maps affinely to [-1, 1]
+    a, b = np.array([0.0, 2.0, -3.0]), np.array([1.0, 5.0, -1.0])
+    Pt = a + (b - a) * (P + 1) / 2
+    assert np.allclose(O.eval_points(c, Pt, a, b), v, atol=1e-12)
+
+
+def test_small_fit_workload_full_oracle_path():
+    """d=2, n=17 coefficients 0.5^(k1+k2) N(0,1): nodal values, refit, grid and points."""
+    w = I.small_fit_workload()
+    c = w["coeffs"]
+    a = lobatto(17)
+    G = npc.chebgrid2d(a, a, c)
+    fit = O.fit_nd(G)
+    assert np.abs(fit - c).max() / np.abs(c).max() < 1e-13
+    g = w["grid"][0]
+    D = O.eval_grid(fit, [g, g])
+    assert np.abs(D - npc.chebgrid2d(g, g, c)).max() / np.abs(D).max() < 1e-13
+    P = w["points"]
+    v = O.eval_points(fit, P)
+    assert np.abs(v - npc.chebval2d(P[:, 0], P[:, 1], c)).max() / np.abs(v).max() < 1e-13
+
+
+# ---- Section 2.1 / 3.4: the game ----------------------------------------------
+
+def lq_values(lq, r, pb):
+    J = pb.shape[1]
+    V = np.empty((J, pb.shape[0]))
+    U = np.empty((J, pb.shape[0]))
+    for i in range(J):
+        Q, b, a = lq["Q"][r, i], lq["b"][r, i], lq["a"][r, i]
+        V[i] = 0.5 * np.einsum("nj,jk,nk->n", pb, Q, pb) + pb @ b + a
+        U[i] = pb @ lq["F"][r, i] + lq["f"][r, i]
+    return V, U
+
+
+@pytest.mark.parametrize("J", [2, 3, 4])
+def test_game_iteration_equals_lq_recursion(J):
+    """While the bounds are inactive every iterate is the J x J LQ recursion's quadratic."""
+    p = I.draw_game_params(I.SplitMix64(100 + J), J)
+    n = 4 if J == 4 else 5
+    R = 6
+    opts = O.make_opts(n, h=1e-2, P_M=0.25, U_M=1.0, tol=0.0, max_iter=R)
+    res = O.game_solve(p, opts)
+    assert res["iters"] == R
+    lq = O.game_lq(p, 1e-2, R)
+    pb, _ = O.game_nodes(opts, J)
+    V, U = lq_values(lq, R - 1, pb)
+    assert (U > 0).all() and (U < 1).all()        # bounds inactive: the pin applies
+    assert np.abs(res["Vnod"] - V).max() <= 1e-12 * np.abs(V).max()
+    assert np.abs(res["u"] - U).max() <= 1e-12
+    # and the coefficients: refit of a quadratic has nothing beyond degree 2
+    Vc = res["Vcoef"].reshape((J,) + (n,) * J)
+    for i in range(J):
+        hi = np.indices((n,) * J).sum(axis=0) > 2
+        assert np.abs(Vc[i][hi]).max() < 1e-14
+
+
+def test_lq_recursion_first_step_and_fixed_point_bellman():
+    """r=1 from V=0: u=A, V = h(A^2/2 - phi p_i^2 / 2); the fixed point satisfies Bellman's equation."""
+    p = I.game_params(2)
+    h = 1e-2
+    lq = O.game_lq(p, h, 1)
+    for i in range(2):
+        Q = np.zeros((2, 2))
+        Q[i, i] = -h * p["phi"][i]
+        assert np.allclose(lq["Q"][0, i], Q, atol=1e-15)
+        assert np.allclose(lq["b"][0, i], 0, atol=1e-15)
+        assert abs(lq["a"][0, i] - h * p["A"][i] ** 2 / 2) < 1e-15
+        assert np.allclose(lq["F"][0, i], 0) and abs(lq["f"][0, i] - p["A"][i]) < 1e-15
+    R = 6000
+    lq = O.game_lq(p, h, R)
+    delta = 1 - p["rho"] * h
+    rng = np.random.default_rng(5)
+    ug = np.linspace(0, 1, 200001)
+    for _ in range(5):
+        x = rng.uniform(0, 0.5, 2)
+        for i in range(2):
+            Q, b, a = lq["Q"][-1, i], lq["b"][-1, i], lq["a"][-1, i]
+            Vf = lambda q: 0.5 * q @ Q @ q + b @ q + a
+            j = 1 - i
+            uj = lq["F"][-1, j] @ x + lq["f"][-1, j]
+            best = -np.inf
+            g0 = I.neighbour_matrix(2) @ x - p["c"] * x
+            for ui in (ug,):
+                u = np.zeros((ui.size, 2))
+                u[:, i] = ui
+                u[:, j] = uj
+                q = x + h * (g0 + p["beta"] * u)
+                vals = h * (ui * (p["A"][i] - ui / 2) - p["phi"][i] / 2 * x[i] ** 2) + \
+                    delta * (0.5 * np.einsum("nj,jk,nk->n", q, Q, q) + q @ b + a)
+                best = vals.max()
+            assert abs(best - Vf(x)) < 1e-9
+
+
+def test_game_symmetric_players_coincide():
+    """Paper Section 4.2: players 1 and 3 of the 3-region chain are symmetric."""
+    p = I.game_params(3, A=[0.45, 0.55, 0.45], phi=[0.9, 1.2, 0.9])
+    n = 5
+    opts = O.make_opts(n, h=1e-2, P_M=1.0, U_M=1.0, tol=0.0, max_iter=40)
+    res = O.game_solve(p, opts)
+    V = res["Vnod"].reshape(3, n, n, n)
+    U = res["u"].reshape(3, n, n, n)
+    assert np.abs(V[0] - V[2].transpose(2, 1, 0)).max() < 1e-13
+    assert np.abs(U[0] - U[2].transpose(2, 1, 0)).max() < 1e-12
+
+
+def test_game_contraction_rate_is_delta():
+    p = I.single_game_workload()
+    opts = O.make_opts(5, h=1e-2, P_M=1.0, U_M=1.0, tol=0.0, max_iter=1200)
+    res = O.game_solve(p, opts, history=True)
+    h = res["history"]
+    ratio = h[-1] / h[-2]
+    assert abs(ratio - (1 - p["rho"] * 1e-2)) < 1e-5
+    assert (np.diff(h[200:]) < 0).all()
+
+
+def test_game_dynamics_reading():
+    """g_i = (1/m) sum_{j != i} k_ij (p_j - p_i) - c_i p_i + beta_i u_i; uniform p has no diffusion."""
+    p = I.game_params(3)
+    g = O.game_dynamics(p, [0.3, 0.3, 0.3], [0.1, 0.2, 0.0])
+    assert np.allclose(g, -0.5 * 0.3 + np.array([0.1, 0.2, 0.0]))
+    g = O.game_dynamics(p, [1.0, 0.0, 0.0], [0, 0, 0])
+    assert np.allclose(g, [-1.0 - 0.5, 1.0, 0.0])      # pollution flows from 1 to its neighbour 2
+
+
+def test_game_node_update_matches_direct_maximisation():
+    """Steps 1-3 at one node: the C1v interpolant's maximiser vs a brute-force search of W(u)."""
+    p = I.single_game_workload()
+    n = 5
+    J = 3
+    opts = O.make_opts(n, h=1e-2, P_M=1.0, U_M=1.0, tol=0.0, max_iter=30)
+    res = O.game_solve(p, opts)
+    pb, _ = O.game_nodes(opts, J)
+    delta = 1 - p["rho"] * 1e-2
+    ug = np.linspace(0, 1, 100001)
+    for j in (0, 17, 62, 124):
+        for i in range(J):
+            uo = res["u"][:, j]
+            us, vs, inside, conc = O.game_node_update(p, opts, i, pb[j], uo, res["Vcoef"][i])
+            vals = []
+            for u in ug[::100]:
+                uu = uo.copy()
+                uu[i] = u
+                q = pb[j] + 1e-2 * O.game_dynamics(p, pb[j], uu)
+                xr = 2 * q - 1
+                Vq = O.eval_direct(res["Vcoef"][i].reshape(n, n, n), xr)
+                vals.append(1e-2 * (u * (p["A"][i] - u / 2) - p["phi"][i] / 2 * pb[j][i] ** 2) + delta * Vq)
+            vals = np.array(vals)
+            assert vs >= vals.max() - 1e-15
+            assert abs(vs - vals.max()) < 2e-9      # grid step 1e-3: h (1e-3)^2 / 8 bound
