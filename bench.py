@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the tensorial Chebyshev hot path on GB300.
+
+Workload (one step): the d=4, n=33 coefficient tensor c_k = N(0,1) 0.7^|k|_1
+(seed 1) evaluated on the 64^4 uniform tensor grid (16,777,216 points) with
+cheb_eval_grid in the headline split form, inputs resident in HBM. Reported
+next to it: the same evaluation through the FP64 CUDA-core path, the error of
+each against the FP64 path and against the CPU oracle on a sample, the
+roofline of the dominant kernel, the FP64 fit of the 33^4 nodal tensor, and
+the CPU oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 it runs under torchrun, one rank per GPU; every rank evaluates its
+own grid (independent replicas, no collective on the data path) and the
+value is the total evaluations of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Chebyshev evals/sec and game solves/sec on 1 GB300 vs FP64 GPU path, at stated error"
+WORKLOAD = "tensor grid d=4 n=33 (1,185,921 coefficients) on 64^4 = 16,777,216 points"
+HEADLINE_FORM = "bf16x6"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default=HEADLINE_FORM)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- the oracle as the CPU baseline / reference arm -------------------------------
+
+def oracle_grid_sample(c, grid, target_s=10.0, slab=4):
+    """Oracle tensor-grid evaluation on slabs of the grid (first mode cut to `slab` points)
+    repeated for about target_s seconds on all host cores; returns (evals/s, cores, sample)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    sub = [grid[0][:slab]] + list(grid[1:])
+    per = slab * np.prod([g.size for g in grid[1:]])
+    done, t0 = 0, time.perf_counter()
+    out = None
+    while True:
+        out = O.eval_grid(c, sub)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    return per * done / el, O.get_threads(), f"{done} x oracle eval_grid of a {slab}x64x64x64 slab", out
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from paper_2307_04688_gb300 import inputs as I
+    import oracle as O
+    O.build()
+    w = I.tensor_grid_workload()
+    c, grid = w["coeffs"], w["grid"]
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    sub = [grid[0][:2]] + list(grid[1:])
+    per = 2 * 64 ** 3
+    for _ in range(args.warmup):
+        O.eval_grid(c, sub)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.eval_grid(c, sub)
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    val = per * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seed 1)",
+            "config": {"workload": WORKLOAD, "sample": "2x64x64x64 slab per step",
+                       "arithmetic": "FP64 CPU oracle, nested mode products, OpenMP"},
+            "cpu_baseline": {"value": val, "unit": "evals/s", "cores": O.get_threads(), "kind": "oracle",
+                             "sample": f"per step: oracle eval_grid of a 2x64x64x64 slab ({per} evals)"},
+            "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---- our arm -------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_2307_04688_gb300 as cb
+    from paper_2307_04688_gb300 import build as B
+    from paper_2307_04688_gb300 import inputs as I
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    ctx = cb.Context(local)
+    w = I.tensor_grid_workload()
+    c_np, grid = w["coeffs"], w["grid"]
+    c = torch.from_numpy(c_np).cuda()
+    xs = [torch.from_numpy(g).cuda() for g in grid]
+    evals = 64 ** 4
+    form = args.form
+    out = torch.empty((64,) * 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+
+    def timed(fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if profile:
+            ctx.profile(True)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        barrier(world)
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile(False)
+        return max_over_ranks(tot / steps, world), prof
+
+    # headline: split form, device-resident inputs
+    with ClockSampler(local) as clk:
+        ms, prof = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec=form, out=out), args.steps,
+                         args.warmup, profile=True)
+    clocks = clk.summary()
+    value = world * evals / (ms * 1e-3)
+    launches_per_step = sum(v[0] for v in prof.values()) / args.steps
+
+    # roofline of the dominant kernel (largest summed time); its name carries R, n, m
+    hbm, bf16, src = peaks()
+    dom_name, (dom_n, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    kv = dict(t.split("=") for t in dom_name.split()[1:])
+    R, n_, m_ = int(kv["R"]), int(kv["n"]), int(kv["m"])
+    in_bytes = 8 if kv.get("x") == "f64" else 4
+    alg_bytes = in_bytes * R * n_ + 4 * R * m_          # X read once, output written once (FP32)
+    per_launch_ms = dom_ms / dom_n
+    # FP64 path on the same grid (the comparison the metric names)
+    out64 = torch.empty((64,) * 4, dtype=torch.float64, device="cuda")
+    ms64, prof64 = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec="fp64", out=out64),
+                         max(2, args.steps // 10), 2, profile=True)
+    err_vs_fp64 = float(((out.double() - out64).abs().max() / out64.abs().max()).item())
+    # the other split forms (error and time)
+    forms = {}
+    for f in ("tf32x3", "bf16x3", "bf16x6"):
+        o = torch.empty_like(out)
+        msf, _ = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec=f, out=o), max(3, args.steps // 4), 2)
+        forms[f] = {"ms": msf, "evals_per_s": world * evals / (msf * 1e-3),
+                    "max_norm_err_vs_fp64_path": float(((o.double() - out64).abs().max() /
+                                                        out64.abs().max()).item())}
+    # the FP64 fit of the 33^4 nodal tensor (cheb_fit)
+    nod = out64[:33, :33, :33, :33].contiguous()
+    msfit, _ = timed(lambda: cb.cheb_fit(ctx, nod), 5, 2)
+
+    # end to end: host (pinned) coefficients in, host result out, through the public call
+    c_host = torch.from_numpy(c_np).pin_memory()
+    out_host = torch.empty((64,) * 4, dtype=torch.float32).pin_memory()
+    c_dev = torch.empty_like(c)
+
+    def e2e_step():
+        c_dev.copy_(c_host, non_blocking=True)
+        cb.cheb_eval_grid(ctx, c_dev, xs, prec=form, out=out)
+        out_host.copy_(out, non_blocking=True)
+
+    ms_e2e, _ = timed(e2e_step, max(3, args.steps // 2), 2)
+    h2d = c_host.numel() * 8 + sum(g.size * 8 for g in grid) * 0
+    d2h = out_host.numel() * 4
+
+    result = None
+    if rank == 0:
+        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x6->f32" if form == "bf16x6" else form, "data": "synthetic (seed 1)",
+            "config": {"workload": WORKLOAD, "form": form, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "error": {"max_norm_vs_fp64_gpu_path": err_vs_fp64},
+            "fp64_path": {"ms_per_step": ms64, "evals_per_s": world * evals / (ms64 * 1e-3),
+                          "speedup_of_split": ms64 / ms},
+            "forms": forms,
+            "fit_fp64_33^4": {"ms": msfit},
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "peak_source": src,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "per_launch_ms": per_launch_ms,
+                         "note": "dominant kernel = one mode product; algorithmic bytes = its input "
+                                 "rows read once + its FP32 output written once"},
+            "kernel_times_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "gpu_launches": launches_per_step,
+            "clocks": clocks,
+            "e2e": {"value": world * evals / (ms_e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        }
+        if not args.no_cpu and world == 1:
+            val, cores, sample, ref_slab = oracle_grid_sample(c_np, grid, target_s=10.0)
+            gpu_slab = out[:4].double().cpu().numpy()
+            line["cpu_baseline"] = {"value": val, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+            line["error"]["max_norm_vs_oracle_sample"] = float(np.abs(gpu_slab - ref_slab).max() /
+                                                               np.abs(ref_slab).max())
+        result = line
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

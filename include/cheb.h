@@ -1,0 +1,250 @@
+/*
+ * cheb.h - C ABI of libcheb, a GB300 (sm_103a) implementation of the
+ * tensorial Chebyshev method of de Castro, Gaton & Gomez, "A tensorial-
+ * parallel Chebyshev method for a differential game theory problem"
+ * (arXiv 2307.04688).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * - Tensors are dense and row-major: the LAST mode varies fastest. (The paper
+ *   stores them column-major with the first mode fastest, Section 3.1.)
+ * - Mode s of a coefficient or nodal tensor has n[s] = N_s + 1 entries. Node
+ *   k of that mode is the Chebyshev-Lobatto point alpha^k = cos(pi k / N_s)
+ *   of [-1, 1] (Section 3.1), so k = 0 is x = +1 and the nodes descend.
+ * - "Device" pointers are CUDA device (or managed) memory on the context's
+ *   device, owned by the caller; "host" pointers are ordinary host memory,
+ *   read during the call only. The library never frees caller memory.
+ * - Every call that takes a `stream` (a cudaStream_t passed as void*, NULL
+ *   for the legacy default stream) is stream-ordered: it enqueues work and
+ *   returns without waiting, unless stated otherwise.
+ * - Argument errors are detected on the host before anything is enqueued
+ *   and return CHEB_EINVAL (or CHEB_EUNSUPPORTED for valid shapes the
+ *   library does not implement). There is no CPU fallback. The message of
+ *   the last failure on the calling thread is returned by cheb_last_error().
+ */
+#ifndef CHEB_H
+#define CHEB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CHEB_API __attribute__((visibility("default")))
+#else
+#define CHEB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHEB_OK = 0,
+    CHEB_EINVAL = 1,        /* bad argument (null pointer, bad size, bad domain) */
+    CHEB_ENOMEM = 2,        /* device workspace allocation failed */
+    CHEB_ECUDA = 3,         /* a CUDA runtime call failed */
+    CHEB_ENOCONV = 4,       /* game: max_iter reached before the tolerance */
+    CHEB_ESTALL = 5,        /* game: residual stopped decreasing above the tolerance */
+    CHEB_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
+    CHEB_EUNSUPPORTED = 7   /* valid request outside the implemented shapes */
+} cheb_status;
+
+/* Arithmetic of the mode products.
+ *  CHEB_FP64    FP64 on the CUDA cores.
+ *  CHEB_TF32X3  tensor cores, kind::tf32: each operand split x = hi + lo into
+ *               two TF32 numbers, products hi*hi + hi*lo + lo*hi, FP32
+ *               accumulation.
+ *  CHEB_BF16X3  tensor cores, kind::f16 with BF16 inputs: two-way split, the
+ *               same three products, FP32 accumulation.
+ *  CHEB_BF16X6  three-way BF16 split x = x0 + x1 + x2, the six products with
+ *               i + j <= 2, FP32 accumulation.
+ * The split forms return FP32 results. */
+typedef enum {
+    CHEB_FP64 = 0,
+    CHEB_TF32X3 = 1,
+    CHEB_BF16X3 = 2,
+    CHEB_BF16X6 = 3
+} cheb_precision;
+
+typedef struct cheb_ctx cheb_ctx;
+
+/* Create a context on CUDA device `device`. The context owns device
+ * workspaces, cached matrices and CUDA graphs; it is not thread-safe (use
+ * one context per host thread). Returns CHEB_EINVAL for a null `ctx` or a
+ * bad device ordinal, CHEB_ECUDA if the device cannot be used. */
+CHEB_API cheb_status cheb_create(cheb_ctx **ctx, int device);
+
+/* Synchronise the device, then free everything the context owns. */
+CHEB_API cheb_status cheb_destroy(cheb_ctx *ctx);
+
+/* Message of the last failed call on this host thread ("" if none). The
+ * string stays valid until the next call on the same thread. */
+CHEB_API const char *cheb_last_error(void);
+
+/* Library version as "major.minor.patch". */
+CHEB_API const char *cheb_version(void);
+
+/* Wait for all work on the context's device, then report and clear the
+ * device error word that bounded device-side waits write when they run out
+ * (CHEB_ETIMEOUT). Returns CHEB_OK if no kernel reported a failure. */
+CHEB_API cheb_status cheb_device_status(cheb_ctx *ctx);
+
+/* Kernel timing. With profiling on, the library brackets every kernel it
+ * launches with CUDA events on the launch stream (the stream the caller
+ * passed) and accumulates, per kernel name, the launch count and the summed
+ * device time. cheb_profile(ctx, 1) clears the totals and turns timing on;
+ * cheb_profile(ctx, 0) clears and turns it off. cheb_profile_count waits for
+ * the recorded events and returns the number of kernel names (-1 on a bad
+ * context); cheb_profile_get copies entry `idx` (0-based, sorted by name):
+ * its name into `name` (NUL-terminated, at most name_len bytes), its launch
+ * count and its total time in milliseconds. Not for use inside stream
+ * capture. */
+CHEB_API cheb_status cheb_profile(cheb_ctx *ctx, int enable);
+CHEB_API int cheb_profile_count(cheb_ctx *ctx);
+CHEB_API cheb_status cheb_profile_get(cheb_ctx *ctx, int idx, char *name, int name_len,
+                                      int64_t *launches, double *total_ms);
+
+/*
+ * cheb_fit - coefficients of the d-dimensional Chebyshev interpolant.
+ *
+ * Section 3.1, Definition 3.2 with eq. (forcoef) and Algorithm Cnv: given the
+ * values Gamma(k_1..k_d) = F(alpha^{k_1}_1, ..., alpha^{k_d}_d) at the tensor
+ * grid of Chebyshev-Lobatto nodes, returns the coefficients p_l of
+ * I_N F(x) = sum_l p_l T_{l_1}(x_1)...T_{l_d}(x_d). Each mode is one product
+ * with the n_s x n_s matrix M[l,k] = (2/N) s_l s_k cos(pi l k / N),
+ * s_0 = s_N = 1/2 and s = 1 otherwise (eq. (forcoef) in matrix form, which is
+ * what Algorithm C1v computes with an FFT).
+ *
+ *  d       number of modes, 1 <= d <= 6
+ *  n       host [d]; n[s] = N_s + 1 nodes of mode s, 2 <= n[s] <= 64
+ *  values  device, prod(n) doubles, row-major, node k = 0 <-> x = +1
+ *  coeffs  device, prod(n) doubles, row-major, coefficient index l_s per mode;
+ *          may equal `values` (in place) but must not partially overlap it
+ *  stream  CUDA stream
+ * Arithmetic: FP64 on the CUDA cores.
+ */
+CHEB_API cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *values,
+                     double *coeffs, void *stream);
+
+/*
+ * cheb_eval_grid - evaluate an interpolant on a tensor grid of points.
+ *
+ * Section 3.2: D(j_1..j_d) = I_N F(b^1_{j_1}, ..., b^d_{j_d}), computed as d
+ * successive mode products of the coefficient tensor with the matrices
+ * B_s(j, l) = T_l(b^s_j) (m_s x n_s).
+ *
+ *  d, n    as in cheb_fit
+ *  coeffs  device, prod(n) doubles (output of cheb_fit)
+ *  a, b    host [d]; the interpolant lives on prod_s [a_s, b_s], a_s < b_s;
+ *          a point t of mode s is mapped to x = (2t - a_s - b_s) / (b_s - a_s)
+ *  m       host [d]; points per mode, 1 <= m[s] <= 4096
+ *  x       host array of d device pointers; x[s] holds m[s] doubles. Points
+ *          outside [a_s, b_s] are allowed (the polynomial is continued by the
+ *          three-term recurrence).
+ *  out     device, prod(m) values, row-major in (j_1..j_d): doubles for
+ *          CHEB_FP64, floats for the split forms
+ *  prec    arithmetic of the mode products (see cheb_precision)
+ * Intermediates live in a context-owned workspace that grows on demand
+ * (CHEB_ENOMEM if that allocation fails).
+ */
+CHEB_API cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                           const double *a, const double *b, const int32_t *m,
+                           const double *const *x, void *out, cheb_precision prec,
+                           void *stream);
+
+/*
+ * cheb_eval_points - evaluate an interpolant at P scattered points.
+ *
+ * Section 3.3 (one polynomial, a different point per evaluation):
+ * f(x_j) = sum_l p_l prod_s T_{l_s}(x_{j,s}). The paper gathers a diagonal
+ * out of a full pagemtimes product; here each point is contracted directly.
+ *
+ *  coeffs  device, prod(n) doubles
+ *  a, b    host [d] domain as in cheb_eval_grid
+ *  P       number of points, 0 <= P <= 2^31 - 1 (P = 0 is a no-op)
+ *  x       device, P x d doubles, row-major (point j at x[j*d .. j*d+d-1])
+ *  out     device, P values: doubles for CHEB_FP64, floats otherwise
+ *  prec    CHEB_FP64 or a split form
+ */
+CHEB_API cheb_status cheb_eval_points(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                             const double *a, const double *b, int64_t P, const double *x,
+                             void *out, cheb_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------
+ * The J-player pollution game (Section 2, linear-quadratic specification,
+ * time step h, Section 2.1):
+ *   g_i(p, u) = (1/m) sum_{j != i} K[i][j] (p_j - p_i) - c_i p_i + beta_i u_i,
+ *   G_i(p, u_i) = u_i (A_i - u_i/2) - (phi_i/2) p_i^2,   delta_h = 1 - rho h,
+ *   V_i(p) = max_{0 <= u_i <= U_M} h G_i + delta_h V_i(p + h g(p, [u_i, u*_{-i}])).
+ * The printed coupling term k_ij (p_i - p_j) is anti-diffusive with k_ij >= 0;
+ * the paper's matrices have zero row sums, and the term is taken as
+ * K[i][j] (p_j - p_i), i.e. (K p)_i / m. Only the off-diagonal of K is used.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t J;          /* players, 1 <= J <= 4 */
+    double K[16];       /* J x J row-major neighbour matrix (off-diagonal >= 0) */
+    double m;           /* common region measure m_i > 0 */
+    double A[4];        /* emission benefit A_i */
+    double beta[4];     /* emission-to-pollution factor beta_i */
+    double phi[4];      /* damage cost phi_i >= 0 */
+    double c[4];        /* natural decay c_i */
+    double rho;         /* discount rate, 0 < rho h < 1 */
+} cheb_game_params;
+
+typedef struct {
+    double h;           /* time step h > 0 */
+    double P_M;         /* state box [0, P_M]^J (Section 3.4, Step 0) */
+    double U_M;         /* control interval [0, U_M] */
+    double tol;         /* stop when max_{i,j} |V^[r+1]_i - V^[r]_i| < tol at the nodes */
+    int32_t n;          /* state nodes per player N^p + 1, 3 <= n <= 33 */
+    int32_t n_u;        /* control nodes N^u + 1; 0 means n. Must be 0 or >= n:
+                           then the control interpolant of Step 2 is exact and the
+                           maximisation runs on the exact one-variable polynomial */
+    int64_t max_iter;   /* iteration cap (CHEB_ENOCONV when reached) */
+    int32_t prec;       /* cheb_precision of the evaluation products */
+    int32_t polish_fp64;/* split forms: 1 = continue in FP64 once the split
+                           iteration stagnates, so that tol is reached in FP64 */
+} cheb_game_opts;
+
+typedef struct {
+    double *V;          /* device, J x n^J: coefficient tensors of V_1..V_J on
+                           return (player-major, each tensor row-major) */
+    double *u;          /* device, J x n^J: nodal controls u_i(pbar_j) on return */
+    const double *V0;   /* device or NULL: initial NODAL values J x n^J (zero if NULL) */
+    const double *u0;   /* device or NULL: initial nodal controls J x n^J (zero if NULL) */
+    int64_t iters;      /* out: iterations performed */
+    int64_t iters_split;/* out: of which in split precision */
+    double residual;    /* out: last residual */
+    int32_t status;     /* out: cheb_status of this instance */
+} cheb_game_result;
+
+/*
+ * game_solve - solve `batch` independent pollution games with the
+ * Chebyshev collocation iteration (Section 2.1 Steps 0-4; Section 3.4).
+ *
+ * Step 0 fits V^[0] from the initial nodal values. Each iteration, for every
+ * player i and state node pbar_j (all players at once from iterate r):
+ * the next states pbar_j + h g(pbar_j, [u, u^[r]_{-i}(pbar_j)]) are affine in
+ * u, so V^[r]_i along them is a one-variable Chebyshev series in u; its
+ * maximiser over [0, U_M] (Newton with the derivative of Proposition 3.1,
+ * projected, compared with the bounds) gives u^[r+1]_i(pbar_j) and
+ * V^[r+1]_i(pbar_j); then V^[r+1]_i is refitted (cheb_fit) and the residual
+ * max |V^[r+1] - V^[r]| over the nodes is tested against tol (Step 4).
+ *
+ *  batch   number of instances, >= 1
+ *  params  host [batch]
+ *  opts    host [batch]; instances may differ in n
+ *  res     host [batch]; V and u must be distinct device buffers of
+ *          J * n^J doubles each
+ *  stream  CUDA stream
+ * Synchronous: returns after every instance finished; per-instance status,
+ * iteration count and residual are in res[]. The return value is CHEB_OK if
+ * every instance converged, else the first non-OK instance status.
+ */
+CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
+                       const cheb_game_opts *opts, cheb_game_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEB_H */

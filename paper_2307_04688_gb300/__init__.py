@@ -1,0 +1,213 @@
+"""GB300 implementation of the tensorial Chebyshev method (arXiv 2307.04688).
+
+The computation lives in libcheb.so (C ABI, include/cheb.h). This package
+only marshals torch CUDA tensors into those calls; the functions keep the
+C names: cheb_fit, cheb_eval_grid, cheb_eval_points, game_solve.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CHEB_BF16X3, CHEB_BF16X6, CHEB_FP64, CHEB_TF32X3, PRECISIONS, ChebError,
+                   GameOpts, GameParams, GameResult, check, load)
+
+__all__ = ["Context", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
+           "CHEB_FP64", "CHEB_TF32X3", "CHEB_BF16X3", "CHEB_BF16X6", "ChebError", "precision"]
+
+
+def precision(p) -> int:
+    if isinstance(p, str):
+        return PRECISIONS[p.lower()]
+    return int(p)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _i32(v):
+    arr = (C.c_int32 * len(v))(*[int(t) for t in v])
+    return arr
+
+
+def _f64(v):
+    return (C.c_double * len(v))(*[float(t) for t in v])
+
+
+class Context:
+    """A libcheb context on one CUDA device (owns workspaces and caches)."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        self._h = C.c_void_p()
+        check(L.cheb_create(C.byref(self._h), int(device)))
+        self.device = int(device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().cheb_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_status(self) -> None:
+        check(load().cheb_device_status(self._h))
+
+    def profile(self, enable: bool) -> None:
+        """Turn per-kernel CUDA-event timing on or off (clears the totals)."""
+        check(load().cheb_profile(self._h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total milliseconds)} since profiling was turned on."""
+        L = load()
+        cnt = L.cheb_profile_count(self._h)
+        if cnt < 0:
+            check(_lib.CHEB_EINVAL)
+        out = {}
+        for i in range(cnt):
+            buf = C.create_string_buffer(128)
+            nl, ms = C.c_int64(), C.c_double()
+            check(L.cheb_profile_get(self._h, i, buf, 128, C.byref(nl), C.byref(ms)))
+            out[buf.value.decode()] = (int(nl.value), float(ms.value))
+        return out
+
+
+def _need_cuda(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def cheb_fit(ctx: Context, values, coeffs=None, stream=None):
+    """Coefficients of the interpolant of nodal values (float64 tensor, any d <= 6)."""
+    import torch
+    _need_cuda(values, torch.float64, "values")
+    if coeffs is None:
+        coeffs = torch.empty_like(values)
+    _need_cuda(coeffs, torch.float64, "coeffs")
+    n = _i32(values.shape)
+    check(load().cheb_fit(ctx.handle, values.dim(), n, C.c_void_p(values.data_ptr()),
+                          C.c_void_p(coeffs.data_ptr()), _stream_ptr(stream)))
+    return coeffs
+
+
+def cheb_eval_grid(ctx: Context, coeffs, xs, a=None, b=None, prec="fp64", out=None, stream=None):
+    """Values of the interpolant on the tensor grid xs[0] x ... x xs[d-1]."""
+    import torch
+    _need_cuda(coeffs, torch.float64, "coeffs")
+    d = coeffs.dim()
+    if len(xs) != d:
+        raise ValueError("need one point array per mode")
+    for i, x in enumerate(xs):
+        _need_cuda(x, torch.float64, f"xs[{i}]")
+    a = [-1.0] * d if a is None else list(a)
+    b = [1.0] * d if b is None else list(b)
+    p = precision(prec)
+    shape = tuple(int(x.numel()) for x in xs)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64 if p == CHEB_FP64 else torch.float32,
+                          device=coeffs.device)
+    _need_cuda(out, torch.float64 if p == CHEB_FP64 else torch.float32, "out")
+    ptrs = (C.c_void_p * d)(*[x.data_ptr() for x in xs])
+    check(load().cheb_eval_grid(ctx.handle, d, _i32(coeffs.shape), C.c_void_p(coeffs.data_ptr()),
+                                _f64(a), _f64(b), _i32(shape), ptrs, C.c_void_p(out.data_ptr()), p,
+                                _stream_ptr(stream)))
+    return out
+
+
+def cheb_eval_points(ctx: Context, coeffs, x, a=None, b=None, prec="fp64", out=None, stream=None):
+    """Values of the interpolant at the rows of x (P x d, float64)."""
+    import torch
+    _need_cuda(coeffs, torch.float64, "coeffs")
+    _need_cuda(x, torch.float64, "x")
+    d = coeffs.dim()
+    if x.dim() != 2 or x.shape[1] != d:
+        raise ValueError("x must be P x d")
+    a = [-1.0] * d if a is None else list(a)
+    b = [1.0] * d if b is None else list(b)
+    p = precision(prec)
+    P = int(x.shape[0])
+    if out is None:
+        out = torch.empty(P, dtype=torch.float64 if p == CHEB_FP64 else torch.float32,
+                          device=coeffs.device)
+    _need_cuda(out, torch.float64 if p == CHEB_FP64 else torch.float32, "out")
+    check(load().cheb_eval_points(ctx.handle, d, _i32(coeffs.shape), C.c_void_p(coeffs.data_ptr()),
+                                  _f64(a), _f64(b), P, C.c_void_p(x.data_ptr()),
+                                  C.c_void_p(out.data_ptr()), p, _stream_ptr(stream)))
+    return out
+
+
+def game_params(p) -> GameParams:
+    g = GameParams()
+    J = int(p["J"])
+    g.J = J
+    K = np.asarray(p["K"], dtype=np.float64).reshape(J, J)
+    for t in range(J * J):
+        g.K[t] = float(K.flat[t])
+    g.m = float(p["m"])
+    for s in range(J):
+        g.A[s] = float(p["A"][s])
+        g.beta[s] = float(p["beta"][s])
+        g.phi[s] = float(p["phi"][s])
+        g.c[s] = float(p["c"][s])
+    g.rho = float(p["rho"])
+    return g
+
+
+def game_opts(n: int, h: float = 1e-2, P_M: float = 1.0, U_M: float = 1.0, tol: float = 1e-10,
+              max_iter: int = 100000, prec="fp64", polish_fp64: bool = True, n_u: int = 0) -> GameOpts:
+    o = GameOpts()
+    o.h, o.P_M, o.U_M, o.tol = float(h), float(P_M), float(U_M), float(tol)
+    o.n, o.n_u, o.max_iter = int(n), int(n_u), int(max_iter)
+    o.prec = precision(prec)
+    o.polish_fp64 = int(bool(polish_fp64))
+    return o
+
+
+def game_solve(ctx: Context, params, opts, V=None, u=None, V0=None, u0=None, stream=None,
+               raise_on_error: bool = True):
+    """Solve len(params) games; returns (V list, u list, result structs)."""
+    import torch
+    if isinstance(params, dict):
+        params = [params]
+    if isinstance(opts, GameOpts):
+        opts = [opts] * len(params)
+    B = len(params)
+    P = (GameParams * B)(*[game_params(p) for p in params])
+    O = (GameOpts * B)(*opts)
+    R = (GameResult * B)()
+    Vs, us = [], []
+    dev = torch.device("cuda", ctx.device)
+    for i in range(B):
+        J = int(params[i]["J"])
+        NP = int(opts[i].n) ** J
+        Vi = torch.empty((J, NP), dtype=torch.float64, device=dev) if V is None else V[i]
+        ui = torch.empty((J, NP), dtype=torch.float64, device=dev) if u is None else u[i]
+        Vs.append(Vi)
+        us.append(ui)
+        R[i].V = Vi.data_ptr()
+        R[i].u = ui.data_ptr()
+        R[i].V0 = None if V0 is None or V0[i] is None else V0[i].data_ptr()
+        R[i].u0 = None if u0 is None or u0[i] is None else u0[i].data_ptr()
+    st = load().game_solve(ctx.handle, B, P, O, R, _stream_ptr(stream))
+    if raise_on_error and st not in (_lib.CHEB_OK,):
+        check(st)
+    return Vs, us, [R[i] for i in range(B)]

@@ -1,0 +1,83 @@
+"""ctypes binding of libcheb (include/cheb.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library. If libcheb.so is
+missing this module raises instead of falling back to anything else. Tensors
+are torch CUDA tensors; torch provides the device memory and the streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcheb.so")
+
+CHEB_OK, CHEB_EINVAL, CHEB_ENOMEM, CHEB_ECUDA, CHEB_ENOCONV, CHEB_ESTALL, CHEB_ETIMEOUT, \
+    CHEB_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "CHEB_OK", 1: "CHEB_EINVAL", 2: "CHEB_ENOMEM", 3: "CHEB_ECUDA", 4: "CHEB_ENOCONV",
+                5: "CHEB_ESTALL", 6: "CHEB_ETIMEOUT", 7: "CHEB_EUNSUPPORTED"}
+CHEB_FP64, CHEB_TF32X3, CHEB_BF16X3, CHEB_BF16X6 = range(4)
+PRECISIONS = {"fp64": CHEB_FP64, "tf32x3": CHEB_TF32X3, "bf16x3": CHEB_BF16X3, "bf16x6": CHEB_BF16X6}
+
+
+class ChebError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GameParams(C.Structure):
+    _fields_ = [("J", C.c_int32), ("K", C.c_double * 16), ("m", C.c_double),
+                ("A", C.c_double * 4), ("beta", C.c_double * 4), ("phi", C.c_double * 4),
+                ("c", C.c_double * 4), ("rho", C.c_double)]
+
+
+class GameOpts(C.Structure):
+    _fields_ = [("h", C.c_double), ("P_M", C.c_double), ("U_M", C.c_double), ("tol", C.c_double),
+                ("n", C.c_int32), ("n_u", C.c_int32), ("max_iter", C.c_int64), ("prec", C.c_int32),
+                ("polish_fp64", C.c_int32)]
+
+
+class GameResult(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("u", C.c_void_p), ("V0", C.c_void_p), ("u0", C.c_void_p),
+                ("iters", C.c_int64), ("iters_split", C.c_int64), ("residual", C.c_double),
+                ("status", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libcheb.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libcheb.so not found at {LIB_PATH}; run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp, ip = C.c_void_p, C.POINTER(C.c_int32)
+    dp = C.POINTER(C.c_double)
+    L.cheb_create.argtypes = [C.POINTER(vp), C.c_int]
+    L.cheb_destroy.argtypes = [vp]
+    L.cheb_last_error.restype = C.c_char_p
+    L.cheb_version.restype = C.c_char_p
+    L.cheb_device_status.argtypes = [vp]
+    L.cheb_fit.argtypes = [vp, C.c_int, ip, vp, vp, vp]
+    L.cheb_eval_grid.argtypes = [vp, C.c_int, ip, vp, dp, dp, ip, C.POINTER(vp), vp, C.c_int, vp]
+    L.cheb_eval_points.argtypes = [vp, C.c_int, ip, vp, dp, dp, C.c_int64, vp, vp, C.c_int, vp]
+    L.game_solve.argtypes = [vp, C.c_int32, C.POINTER(GameParams), C.POINTER(GameOpts),
+                             C.POINTER(GameResult), vp]
+    L.cheb_profile.argtypes = [vp, C.c_int]
+    L.cheb_profile_count.argtypes = [vp]
+    L.cheb_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double)]
+    for f in ("cheb_profile", "cheb_profile_count", "cheb_profile_get", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid",
+              "cheb_eval_points", "game_solve"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def check(status: int) -> None:
+    if status != CHEB_OK:
+        raise ChebError(status, load().cheb_last_error().decode())

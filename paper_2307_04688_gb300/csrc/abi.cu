@@ -1,0 +1,385 @@
+// C ABI of libcheb: argument checking, workspaces and the mode-product
+// chains behind cheb_fit, cheb_eval_grid and cheb_eval_points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+static thread_local std::string g_last_error;
+thread_local cheb_ctx *tl_ctx = nullptr;
+
+static cudaEvent_t prof_event(cheb_ctx *c)
+{
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(std::string nm, cudaStream_t s) : ctx(tl_ctx), name(std::move(nm)), st(s)
+{
+    if (ctx && ctx->prof_on) {
+        a = prof_event(ctx);
+        b = prof_event(ctx);
+        cudaEventRecord(a, st);
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (a) {
+        cudaEventRecord(b, st);
+        ctx->prof_pending.push_back({name, a, b});
+    }
+}
+
+static void prof_drain(cheb_ctx *c)
+{
+    for (auto &e : c->prof_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(e.b);
+        cudaEventElapsedTime(&ms, e.a, e.b);
+        auto &t = c->prof_totals[e.name];
+        t.first += 1;
+        t.second += ms;
+        c->prof_pool.push_back(e.a);
+        c->prof_pool.push_back(e.b);
+    }
+    c->prof_pending.clear();
+}
+
+cheb_status fail(cheb_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+cheb_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return CHEB_ECUDA;
+}
+
+cheb_status DevBuf::reserve(size_t want)
+{
+    if (want <= bytes) return CHEB_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    size_t sz = want < 256 ? 256 : want;
+    cudaError_t e = cudaMalloc(&ptr, sz);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return fail(CHEB_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    bytes = sz;
+    return CHEB_OK;
+}
+
+void DevBuf::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+// DCT-I matrix of eq. (forcoef): M[l,k] = (c_l / N) w_k cos(pi l k / N) with
+// c_l = 1 for l in {0, N} else 2 and w_k = 1/2 for k in {0, N} else 1, so
+// that p = M F gives the interpolation coefficients. The integer l*k is
+// reduced modulo 2N before the cosine.
+cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out)
+{
+    auto it = ctx->dct.find(n);
+    if (it != ctx->dct.end()) {
+        *out = it->second;
+        return CHEB_OK;
+    }
+    const int N = n - 1;
+    std::vector<double> M((size_t)n * n);
+    for (int l = 0; l < n; ++l)
+        for (int k = 0; k < n; ++k) {
+            const long t = ((long)l * k) % (2L * N);
+            const double cl = (l == 0 || l == N) ? 1.0 : 2.0;
+            const double wk = (k == 0 || k == N) ? 0.5 : 1.0;
+            M[(size_t)l * n + k] = cl / N * wk * std::cos(M_PI * (double)t / (double)N);
+        }
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * M.size());
+    if (e != cudaSuccess) return fail(CHEB_ENOMEM, "dct matrix allocation failed");
+    e = cudaMemcpy(d, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "dct matrix upload");
+    }
+    ctx->dct[n] = d;
+    *out = d;
+    return CHEB_OK;
+}
+
+namespace {
+
+cheb_status check_ctx(cheb_ctx *ctx)
+{
+    tl_ctx = ctx;
+    if (!ctx) return fail(CHEB_EINVAL, "null context");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != ctx->device) CHEB_CUDA_TRY(cudaSetDevice(ctx->device));
+    return CHEB_OK;
+}
+
+cheb_status check_shape(int d, const int32_t *n, int nmax, int64_t *total)
+{
+    if (d < 1 || d > 6) return fail(CHEB_EINVAL, "d must be in [1, 6]");
+    if (!n) return fail(CHEB_EINVAL, "null n");
+    int64_t t = 1;
+    for (int s = 0; s < d; ++s) {
+        if (n[s] < 2 || n[s] > nmax)
+            return fail(CHEB_EINVAL, "n[" + std::to_string(s) + "] must be in [2, " + std::to_string(nmax) + "]");
+        t *= n[s];
+        if (t > (int64_t)1 << 34) return fail(CHEB_EINVAL, "tensor too large");
+    }
+    *total = t;
+    return CHEB_OK;
+}
+
+cheb_status check_domain(int d, const double *a, const double *b)
+{
+    if (!a || !b) return fail(CHEB_EINVAL, "null domain");
+    for (int s = 0; s < d; ++s)
+        if (!(std::isfinite(a[s]) && std::isfinite(b[s]) && a[s] < b[s]))
+            return fail(CHEB_EINVAL, "domain must satisfy a[s] < b[s], finite");
+    return CHEB_OK;
+}
+
+}  // namespace
+}  // namespace cheb
+
+using namespace cheb;
+
+extern "C" {
+
+const char *cheb_last_error(void) { return g_last_error.c_str(); }
+
+const char *cheb_version(void) { return "0.1.0"; }
+
+cheb_status cheb_create(cheb_ctx **ctx, int device)
+{
+    if (!ctx) return fail(CHEB_EINVAL, "null ctx pointer");
+    *ctx = nullptr;
+    int count = 0;
+    CHEB_CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(CHEB_EINVAL, "bad device ordinal");
+    CHEB_CUDA_TRY(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    CHEB_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return fail(CHEB_EUNSUPPORTED, "libcheb needs a Blackwell (sm_10x) GPU");
+    cheb_ctx *c = new cheb_ctx();
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    cudaError_t e = cudaMalloc(&c->d_error, sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(CHEB_ENOMEM, "error word allocation failed");
+    }
+    cudaMemset(c->d_error, 0, sizeof(int));
+    *ctx = c;
+    return CHEB_OK;
+}
+
+cheb_status cheb_destroy(cheb_ctx *ctx)
+{
+    if (!ctx) return CHEB_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->dct) cudaFree(kv.second);
+    ctx->ws[0].release();
+    ctx->ws[1].release();
+    ctx->tmats.release();
+    ctx->xbuf.release();
+    ctx->game.release();
+    ctx->game_aux.release();
+    if (ctx->d_error) cudaFree(ctx->d_error);
+    prof_drain(ctx);
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    if (tl_ctx == ctx) tl_ctx = nullptr;
+    delete ctx;
+    return CHEB_OK;
+}
+
+cheb_status cheb_device_status(cheb_ctx *ctx)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    CHEB_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    CHEB_CUDA_TRY(cudaMemcpy(&v, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        CHEB_CUDA_TRY(cudaMemset(ctx->d_error, 0, sizeof(int)));
+        return fail((cheb_status)v, "a device-side wait ran out of time");
+    }
+    return CHEB_OK;
+}
+
+cheb_status cheb_profile(cheb_ctx *ctx, int enable)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    prof_drain(ctx);
+    ctx->prof_totals.clear();
+    ctx->prof_on = enable != 0;
+    return CHEB_OK;
+}
+
+int cheb_profile_count(cheb_ctx *ctx)
+{
+    if (check_ctx(ctx)) return -1;
+    prof_drain(ctx);
+    return (int)ctx->prof_totals.size();
+}
+
+cheb_status cheb_profile_get(cheb_ctx *ctx, int idx, char *name, int name_len, int64_t *launches,
+                             double *total_ms)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    prof_drain(ctx);
+    if (idx < 0 || idx >= (int)ctx->prof_totals.size()) return fail(CHEB_EINVAL, "bad profile index");
+    auto it = ctx->prof_totals.begin();
+    std::advance(it, idx);
+    if (name && name_len > 0) {
+        std::strncpy(name, it->first.c_str(), (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = it->second.first;
+    if (total_ms) *total_ms = it->second.second;
+    return CHEB_OK;
+}
+
+cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *values, double *coeffs,
+                     void *stream)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    int64_t total = 0;
+    if ((st = check_shape(d, n, 64, &total))) return st;
+    if (!values || !coeffs) return fail(CHEB_EINVAL, "null values/coeffs");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * (size_t)total;
+    if ((st = ctx->ws[0].reserve(bytes))) return st;
+    if ((st = ctx->ws[1].reserve(bytes))) return st;
+    const double *src = values;
+    if (d == 1 && values == coeffs) {
+        CHEB_CUDA_TRY(cudaMemcpyAsync(ctx->ws[1].ptr, values, bytes, cudaMemcpyDeviceToDevice, s));
+        src = static_cast<const double *>(ctx->ws[1].ptr);
+    }
+    // Rotating products: step t contracts mode d-1-t (the trailing mode of
+    // the current layout) and moves the new index to the front.
+    for (int t = 0; t < d; ++t) {
+        const int mode = d - 1 - t;
+        const double *M = nullptr;
+        if ((st = dct_matrix(ctx, n[mode], &M))) return st;
+        double *dst = (t == d - 1) ? coeffs : static_cast<double *>(ctx->ws[t & 1].ptr);
+        if ((st = modeprod_f64(src, M, dst, total / n[mode], n[mode], n[mode], s))) return st;
+        src = dst;
+    }
+    return CHEB_OK;
+}
+
+cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                           const double *a, const double *b, const int32_t *m,
+                           const double *const *x, void *out, cheb_precision prec, void *stream)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    int64_t total = 0;
+    if ((st = check_shape(d, n, 64, &total))) return st;
+    if ((st = check_domain(d, a, b))) return st;
+    if (!coeffs || !out || !m || !x) return fail(CHEB_EINVAL, "null argument");
+    if (prec < CHEB_FP64 || prec > CHEB_BF16X6) return fail(CHEB_EINVAL, "bad precision");
+    int64_t out_total = 1;
+    for (int s = 0; s < d; ++s) {
+        if (m[s] < 1 || m[s] > 4096) return fail(CHEB_EINVAL, "m[s] must be in [1, 4096]");
+        if (!x[s]) return fail(CHEB_EINVAL, "null point array");
+        out_total *= m[s];
+    }
+    if (out_total > ((int64_t)1 << 34)) return fail(CHEB_EINVAL, "grid too large");
+    if (prec != CHEB_FP64) {
+        for (int s = 0; s < d; ++s)
+            if (m[s] > 256) return fail(CHEB_EUNSUPPORTED, "split forms support m[s] <= 256");
+    }
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    const size_t esz = prec == CHEB_FP64 ? sizeof(double) : sizeof(float);
+    // the largest intermediate of the chain (modes d-1..s evaluated)
+    size_t cap = 0;
+    {
+        int64_t cur = total;
+        for (int t = 0; t < d - 1; ++t) {
+            const int mode = d - 1 - t;
+            cur = cur / n[mode] * m[mode];
+            cap = std::max(cap, (size_t)cur * esz);
+        }
+    }
+    size_t toff = 0;
+    for (int s = 0; s < d; ++s) toff += (size_t)m[s] * n[s];
+    if ((st = ctx->tmats.reserve(sizeof(double) * toff))) return st;
+    if (d > 1) {
+        if ((st = ctx->ws[0].reserve(cap))) return st;
+        if ((st = ctx->ws[1].reserve(cap))) return st;
+    }
+    double *T = static_cast<double *>(ctx->tmats.ptr);
+    std::vector<double *> Ts(d);
+    toff = 0;
+    for (int s = 0; s < d; ++s) {
+        Ts[s] = T + toff;
+        toff += (size_t)m[s] * n[s];
+    }
+    if ((st = cheb_matrices(d, x, m, n, a, b, Ts.data(), sm))) return st;
+    const void *src = coeffs;
+    int64_t cur = total;
+    for (int t = 0; t < d; ++t) {
+        const int mode = d - 1 - t;
+        void *dst = (t == d - 1) ? out : ctx->ws[t & 1].ptr;
+        const int64_t R = cur / n[mode];
+        if (prec == CHEB_FP64)
+            st = modeprod_f64(static_cast<const double *>(src), Ts[mode], static_cast<double *>(dst), R,
+                              n[mode], m[mode], sm);
+        else
+            st = modeprod_tc(ctx, src, t == 0, Ts[mode], static_cast<float *>(dst), R, n[mode], m[mode],
+                             prec, sm);
+        if (st) return st;
+        cur = R * m[mode];
+        src = dst;
+    }
+    return CHEB_OK;
+}
+
+cheb_status cheb_eval_points(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                             const double *a, const double *b, int64_t P, const double *x,
+                             void *out, cheb_precision prec, void *stream)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    int64_t total = 0;
+    if ((st = check_shape(d, n, 64, &total))) return st;
+    if ((st = check_domain(d, a, b))) return st;
+    if (P < 0 || P > 0x7fffffffLL) return fail(CHEB_EINVAL, "P must be in [0, 2^31 - 1]");
+    if (P == 0) return CHEB_OK;
+    if (!coeffs || !x || !out) return fail(CHEB_EINVAL, "null argument");
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    if (prec == CHEB_FP64)
+        return eval_points_f64(d, n, coeffs, a, b, P, x, static_cast<double *>(out), sm);
+    if (prec < CHEB_FP64 || prec > CHEB_BF16X6) return fail(CHEB_EINVAL, "bad precision");
+    return eval_points_tc(ctx, d, n, coeffs, a, b, P, x, static_cast<float *>(out), prec, sm);
+}
+
+}  // extern "C"

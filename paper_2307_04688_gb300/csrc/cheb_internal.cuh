@@ -1,0 +1,110 @@
+// Internal declarations shared by the translation units of libcheb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cheb.h"
+
+namespace cheb {
+
+// Record `msg` as the calling thread's last error and return `st`.
+cheb_status fail(cheb_status st, const std::string &msg);
+cheb_status cuda_fail(cudaError_t e, const char *what);
+
+#define CHEB_CUDA_TRY(expr)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (expr);                                             \
+        if (e_ != cudaSuccess) return ::cheb::cuda_fail(e_, #expr);          \
+    } while (0)
+
+// A device buffer owned by the context that only grows.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cheb_status reserve(size_t want);
+    void release();
+};
+
+// The context of the ABI call in progress on this host thread (set by the
+// entry points; read by the launch helpers for profiling and error words).
+extern thread_local cheb_ctx *tl_ctx;
+
+// Records CUDA events around one kernel launch when profiling is on.
+struct ProfScope {
+    cheb_ctx *ctx;
+    std::string name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(std::string nm, cudaStream_t s);
+    ~ProfScope();
+};
+
+}  // namespace cheb
+
+struct cheb_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cheb::DevBuf ws[2];                 // ping-pong intermediates of mode-product chains
+    cheb::DevBuf tmats;                 // Chebyshev matrices T_l(x_j) of one call
+    cheb::DevBuf xbuf;                  // a copy of the fit input for in-place fits
+    std::map<int, double *> dct;        // n -> device n x n DCT-I matrix (FP64)
+    cheb::DevBuf game;                  // game state of one game_solve call
+    cheb::DevBuf game_aux;
+    int *d_error = nullptr;             // device error word written by bounded waits
+    // kernel timing (cheb_profile): events around every library launch
+    bool prof_on = false;
+    struct ProfEvent {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfEvent> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    std::map<std::string, std::pair<int64_t, double>> prof_totals;
+};
+
+namespace cheb {
+
+// ---- kernels (fp64_kernels.cu) ----------------------------------------------
+
+// out[j * R + r] = sum_k B[j * n + k] * X[r * n + k]   (j < m, r < R)
+// One product along the trailing mode of a row-major [R x n] view, with the
+// new mode written in front: applied d times it visits every mode and leaves
+// the modes in their original order.
+cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t R, int n, int m,
+                         cudaStream_t st);
+
+// T[j * n + l] = T_l(x~_j), x~_j = (2 x[j * stride] - a - b) / (b - a), j < m, l < n.
+cheb_status cheb_matrix(const double *x, int64_t stride, int64_t m, int n, double a, double b,
+                        double *T, cudaStream_t st);
+
+// The d matrices T_s[j * n_s + l] = T_l(x~_{s,j}) of a tensor grid, one launch.
+cheb_status cheb_matrices(int d, const double *const *x, const int32_t *m, const int32_t *n,
+                          const double *a, const double *b, double *const *T, cudaStream_t st);
+
+// Split-precision point evaluation: the trailing mode on the tensor cores
+// (modeprod_tc with the T rows as the A operand), the rest per point in FP64.
+cheb_status eval_points_tc(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                           const double *a, const double *b, int64_t P, const double *x, float *out,
+                           cheb_precision prec, cudaStream_t st);
+
+// FP64 point evaluation: out[j] = sum_l c_l prod_s T_{l_s}(x~_{j,s}).
+cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const double *a,
+                            const double *b, int64_t P, const double *x, double *out,
+                            cudaStream_t st);
+
+// ---- tensor-core split-precision mode product (tc_modeprod.cu) -------------
+
+// The same product as modeprod_f64 on the tensor cores. X is FP64 when
+// x_f64 != 0 and FP32 otherwise; B is FP64 (split on the fly); out is FP32.
+cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
+                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st);
+
+// Host-side DCT-I matrix of eq. (forcoef), cached per n on the context.
+cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out);
+
+}  // namespace cheb

@@ -1,0 +1,321 @@
+// FP64 CUDA-core kernels: the mode product used by the fit and by the FP64
+// grid evaluation, the Chebyshev matrices T_l(x_j), and FP64 point
+// evaluation. On GB300 the FP64 pipe is the bound for all of them.
+#include <algorithm>
+#include <string>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+namespace {
+
+constexpr int kF64Rows = 64;      // rows r of a tile
+constexpr int kF64Cols = 32;      // output columns j of a tile
+constexpr int kF64Threads = 256;  // 64 rows x 4 column groups, 8 columns each
+constexpr int kMaxN = 64;
+
+// Mode product on a row-major [R x n] view (Section 3.2, one pagemtimes
+// step): out[j * R + r] = sum_k B[j, k] X[r, k]. A block owns 64 rows and
+// 32 output columns. X rows are staged with an odd stride so that the 64-bit
+// shared loads of consecutive rows fall in different banks; B is read as a
+// broadcast. Output stores are coalesced along r.
+__global__ void __launch_bounds__(kF64Threads)
+modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
+                    double *__restrict__ out, int64_t R, int n, int m)
+{
+    extern __shared__ double smem[];
+    const int ns = n | 1;
+    double *sX = smem;
+    double *sB = smem + kF64Rows * ns;
+    const int64_t r0 = (int64_t)blockIdx.x * kF64Rows;
+    const int j0 = blockIdx.y * kF64Cols;
+    const int rows = (int)((R - r0) < kF64Rows ? (R - r0) : kF64Rows);
+    const double *Xt = X + r0 * n;
+    for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
+        int rr = t / n, k = t - rr * n;
+        sX[rr * ns + k] = Xt[t];
+    }
+    for (int t = threadIdx.x; t < (kF64Rows - rows) * n; t += blockDim.x) {
+        int rr = rows + t / n, k = t % n;
+        sX[rr * ns + k] = 0.0;
+    }
+    for (int t = threadIdx.x; t < kF64Cols * n; t += blockDim.x) {
+        int jj = t / n, k = t - jj * n;
+        sB[t] = (j0 + jj < m) ? B[(int64_t)(j0 + jj) * n + k] : 0.0;
+    }
+    __syncthreads();
+    const int tr = threadIdx.x & (kF64Rows - 1);
+    const int tj = threadIdx.x / kF64Rows;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double xv = sX[tr * ns + k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fma(sB[(tj + 4 * q) * n + k], xv, acc[q]);
+    }
+    if (tr < rows) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + tj + 4 * q;
+            if (j < m) out[(int64_t)j * R + r0 + tr] = acc[q];
+        }
+    }
+}
+
+// T[j * n + l] = T_l(x~_j) by the three-term recurrence (valid off [-1,1]).
+__global__ void cheb_matrix_kernel(const double *__restrict__ x, int64_t stride, int64_t m, int n,
+                                   double a, double b, double *__restrict__ T)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const double xr = (2.0 * x[j * stride] - (a + b)) / (b - a);
+    double *Tj = T + (int64_t)j * n;
+    double t0 = 1.0, t1 = xr;
+    Tj[0] = 1.0;
+    if (n > 1) Tj[1] = xr;
+    for (int l = 2; l < n; ++l) {
+        const double t2 = 2.0 * xr * t1 - t0;
+        Tj[l] = t2;
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
+struct ModeMats {
+    const double *x[6];
+    double *T[6];
+    int m[6], n[6];
+    double a[6], b[6];
+};
+
+// All d Chebyshev matrices of a grid evaluation in one launch: blockIdx.y is
+// the mode, T_s[j * n_s + l] = T_l(x~_{s,j}) by the recurrence.
+__global__ void cheb_matrices_kernel(ModeMats M)
+{
+    const int s = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M.m[s]) return;
+    const double xr = (2.0 * M.x[s][j] - (M.a[s] + M.b[s])) / (M.b[s] - M.a[s]);
+    double *Tj = M.T[s] + (int64_t)j * M.n[s];
+    double t0 = 1.0, t1 = xr;
+    Tj[0] = 1.0;
+    if (M.n[s] > 1) Tj[1] = xr;
+    for (int l = 2; l < M.n[s]; ++l) {
+        const double t2 = 2.0 * xr * t1 - t0;
+        Tj[l] = t2;
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
+struct PointDims {
+    int d;
+    int n[6];
+    double a[6], b[6];
+};
+
+// One thread per point: T values per mode, then the nested contraction
+// sum_{l_1} T(x_1) ( sum_{l_2} T(x_2) ( ... sum_{l_d} c_l T(x_d) ) ) with the
+// innermost mode contiguous in memory. All threads of a warp read the same
+// coefficients at the same time (broadcast through L1).
+__global__ void eval_points_f64_kernel(PointDims D, const double *__restrict__ c, int64_t P,
+                                       const double *__restrict__ x, double *__restrict__ out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const int d = D.d;
+    double T[6 * kMaxN];
+    for (int s = 0; s < d; ++s) {
+        const double xr = (2.0 * x[j * d + s] - (D.a[s] + D.b[s])) / (D.b[s] - D.a[s]);
+        double *Ts = T + s * kMaxN;
+        Ts[0] = 1.0;
+        if (D.n[s] > 1) Ts[1] = xr;
+        for (int l = 2; l < D.n[s]; ++l) Ts[l] = 2.0 * xr * Ts[l - 1] - Ts[l - 2];
+    }
+    int64_t outer = 1;
+    for (int s = 0; s < d - 1; ++s) outer *= D.n[s];
+    const int nl = D.n[d - 1];
+    const double *Tl = T + (d - 1) * kMaxN;
+    double part[6] = {0, 0, 0, 0, 0, 0};
+    int idx[6] = {0, 0, 0, 0, 0, 0};
+    double result = 0.0;
+    const double *cp = c;
+    for (int64_t o = 0; o < outer; ++o) {
+        double t = 0.0;
+        for (int k = 0; k < nl; ++k) t = fma(cp[k], Tl[k], t);
+        cp += nl;
+        int s = d - 2;
+        double v = t;
+        while (s >= 0) {
+            part[s] = fma(T[s * kMaxN + idx[s]], v, part[s]);
+            if (++idx[s] < D.n[s]) break;
+            idx[s] = 0;
+            v = part[s];
+            part[s] = 0.0;
+            --s;
+        }
+        if (s < 0) result = v;
+    }
+    out[j] = result;
+}
+
+// Second half of the split-precision point evaluation: Y holds, for every
+// point j, the partial sums over the last mode, Y[q * P + j] with q the flat
+// index of (l_1..l_{d-1}). Each thread finishes its point with the nested
+// contraction over modes 1..d-1 in FP64.
+__global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y, int64_t P,
+                                        const double *__restrict__ x, float *__restrict__ out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const int d = D.d;
+    const int dm = d - 1;               // modes still to contract
+    if (dm == 0) {
+        out[j] = Y[j];
+        return;
+    }
+    double T[5 * kMaxN];
+    for (int s = 0; s < dm; ++s) {
+        const double xr = (2.0 * x[j * d + s] - (D.a[s] + D.b[s])) / (D.b[s] - D.a[s]);
+        double *Ts = T + s * kMaxN;
+        Ts[0] = 1.0;
+        if (D.n[s] > 1) Ts[1] = xr;
+        for (int l = 2; l < D.n[s]; ++l) Ts[l] = 2.0 * xr * Ts[l - 1] - Ts[l - 2];
+    }
+    int64_t outer = 1;
+    for (int s = 0; s < dm - 1; ++s) outer *= D.n[s];
+    const int nl = D.n[dm - 1];
+    const double *Tl = T + (dm - 1) * kMaxN;
+    double part[6] = {0, 0, 0, 0, 0, 0};
+    int idx[6] = {0, 0, 0, 0, 0, 0};
+    double result = 0.0;
+    const float *yp = Y + j;
+    for (int64_t o = 0; o < outer; ++o) {
+        double t = 0.0;
+        for (int k = 0; k < nl; ++k) t = fma((double)yp[(int64_t)k * P], Tl[k], t);
+        yp += (int64_t)nl * P;
+        int s = dm - 2;
+        double v = t;
+        while (s >= 0) {
+            part[s] = fma(T[s * kMaxN + idx[s]], v, part[s]);
+            if (++idx[s] < D.n[s]) break;
+            idx[s] = 0;
+            v = part[s];
+            part[s] = 0.0;
+            --s;
+        }
+        if (s < 0) result = v;
+    }
+    out[j] = (float)result;
+}
+
+}  // namespace
+
+cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t R, int n, int m,
+                         cudaStream_t st)
+{
+    if (R <= 0 || m <= 0) return CHEB_OK;
+    if (n < 1 || n > kMaxN) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: n out of range");
+    const int ns = n | 1;
+    const size_t smem = sizeof(double) * (size_t)(kF64Rows * ns + kF64Cols * n);
+    static bool attr_set = false;
+    if (!attr_set) {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(modeprod_f64_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * (kF64Rows * 65 + kF64Cols * 64))));
+        attr_set = true;
+    }
+    const int64_t tiles = (R + kF64Rows - 1) / kF64Rows;
+    if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many rows");
+    dim3 grid((unsigned)tiles, (unsigned)((m + kF64Cols - 1) / kF64Cols));
+    if (grid.y > 65535) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many columns");
+    ProfScope prof("modeprod_f64 R=" + std::to_string(R) + " n=" + std::to_string(n) +
+                       " m=" + std::to_string(m), st);
+    modeprod_f64_kernel<<<grid, kF64Threads, smem, st>>>(X, B, out, R, n, m);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status cheb_matrix(const double *x, int64_t stride, int64_t m, int n, double a, double b,
+                        double *T, cudaStream_t st)
+{
+    if (m <= 0) return CHEB_OK;
+    ProfScope prof("cheb_matrix", st);
+    cheb_matrix_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(x, stride, m, n, a, b, T);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status cheb_matrices(int d, const double *const *x, const int32_t *m, const int32_t *n,
+                          const double *a, const double *b, double *const *T, cudaStream_t st)
+{
+    ModeMats M{};
+    int mmax = 0;
+    for (int s = 0; s < d; ++s) {
+        M.x[s] = x[s];
+        M.T[s] = T[s];
+        M.m[s] = m[s];
+        M.n[s] = n[s];
+        M.a[s] = a[s];
+        M.b[s] = b[s];
+        mmax = std::max(mmax, (int)m[s]);
+    }
+    if (mmax <= 0) return CHEB_OK;
+    ProfScope prof("cheb_matrices", st);
+    cheb_matrices_kernel<<<dim3((unsigned)((mmax + 127) / 128), (unsigned)d), 128, 0, st>>>(M);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status eval_points_tc(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                           const double *a, const double *b, int64_t P, const double *x, float *out,
+                           cheb_precision prec, cudaStream_t st)
+{
+    int64_t rest = 1;
+    for (int s = 0; s < d - 1; ++s) rest *= n[s];
+    if (rest > 256)
+        return fail(CHEB_EUNSUPPORTED, "split point evaluation needs prod(n[0..d-2]) <= 256");
+    const int nl = n[d - 1];
+    cheb_status r;
+    // T rows of the last mode (P x n_d, FP64) and the partial sums Y (rest x P, FP32)
+    if ((r = ctx->ws[0].reserve(sizeof(double) * (size_t)P * nl))) return r;
+    if ((r = ctx->ws[1].reserve(sizeof(float) * (size_t)P * rest))) return r;
+    double *T = static_cast<double *>(ctx->ws[0].ptr);
+    float *Y = static_cast<float *>(ctx->ws[1].ptr);
+    if ((r = cheb_matrix(x + (d - 1), d, P, nl, a[d - 1], b[d - 1], T, st))) return r;
+    if ((r = modeprod_tc(ctx, T, 1, coeffs, Y, P, nl, (int)rest, prec, st))) return r;
+    PointDims D;
+    D.d = d;
+    for (int s = 0; s < 6; ++s) {
+        D.n[s] = s < d ? n[s] : 1;
+        D.a[s] = s < d ? a[s] : -1.0;
+        D.b[s] = s < d ? b[s] : 1.0;
+    }
+    ProfScope prof("rowwise_contract", st);
+    rowwise_contract_kernel<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(D, Y, P, x, out);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const double *a,
+                            const double *b, int64_t P, const double *x, double *out,
+                            cudaStream_t st)
+{
+    if (P <= 0) return CHEB_OK;
+    PointDims D;
+    D.d = d;
+    for (int s = 0; s < 6; ++s) {
+        D.n[s] = s < d ? n[s] : 1;
+        D.a[s] = s < d ? a[s] : -1.0;
+        D.b[s] = s < d ? b[s] : 1.0;
+    }
+    const int threads = 128;
+    const int64_t blocks = (P + threads - 1) / threads;
+    ProfScope prof("eval_points_f64", st);
+    eval_points_f64_kernel<<<(unsigned)blocks, threads, 0, st>>>(D, coeffs, P, x, out);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+}  // namespace cheb

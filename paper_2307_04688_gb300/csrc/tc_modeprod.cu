@@ -1,0 +1,357 @@
+// Split-precision mode product on the tcgen05 tensor cores.
+//
+// One mode product of the tensorial method (Section 3.2: B . A(:, i_2..i_n)
+// for every page, the pagemtimes step) on a row-major [R x n] view:
+//     out[j * R + r] = sum_k B[j, k] X[r, k],   j < m, r < R,
+// i.e. D = X B^T written transposed, so that applying it once per mode visits
+// every mode and leaves the modes in their original order.
+//
+// Design (GB300):
+//  - persistent CTAs of 256 threads (8 warps), two CTAs per SM; a CTA owns a
+//    128-row tile of X at a time;
+//  - the X tile is one contiguous block of global memory, copied to shared
+//    memory by the TMA engine (cp.async.bulk, completion on an mbarrier) one
+//    tile ahead of its use (double buffer);
+//  - two threads per row split the row into S_A BF16 (or TF32) parts in FP32
+//    arithmetic (FP64 inputs are rounded to FP32 first: GB300's FP64 pipe is
+//    far too slow for this) and write them in the no-swizzle K-major
+//    canonical layout; B (m x n, FP64) is split once per CTA the same way;
+//  - one thread issues the split products as tcgen05.mma (M = 128, N = m
+//    rounded up to 16, K = n rounded up to the instruction K) accumulating in
+//    FP32 in TMEM, and commits to an mbarrier;
+//  - the eight warps read TMEM with tcgen05.ld (warp w: lanes 32 (w % 4) ..,
+//    column chunks of 16 alternating between w < 4 and w >= 4) and store the
+//    tile transposed (coalesced along r).
+// Every wait is bounded; a timeout records CHEB_ETIMEOUT in the context's
+// device error word and the CTA drains its copies, frees TMEM and returns.
+#include <algorithm>
+#include <string>
+
+#include "cheb_internal.cuh"
+#include "tc_common.cuh"
+
+namespace cheb {
+namespace {
+
+using namespace tc;
+
+constexpr int kTileM = 128;
+constexpr int kThreads = 256;
+
+template <int FORM> struct Form;
+// BF16x3: x = x0 + x1, products x1*y0 + x0*y1 + x0*y0 (small terms first).
+template <> struct Form<CHEB_BF16X3> {
+    static constexpr int SA = 2, SB = 2, NPROD = 3, EBYTES = 2, FMT = 1;
+    __device__ static constexpr int pa(int p) { return p == 0 ? 1 : 0; }
+    __device__ static constexpr int pb(int p) { return p == 1 ? 1 : 0; }
+};
+// BF16x6: x = x0 + x1 + x2, the six products with i + j <= 2.
+template <> struct Form<CHEB_BF16X6> {
+    static constexpr int SA = 3, SB = 3, NPROD = 6, EBYTES = 2, FMT = 1;
+    __device__ static constexpr int pa(int p)
+    {
+        return p == 0 ? 2 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 1 : p == 4 ? 0 : 0;
+    }
+    __device__ static constexpr int pb(int p)
+    {
+        return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 2 : p == 3 ? 0 : p == 4 ? 1 : 0;
+    }
+};
+// TF32x3: x = x0 + x1 in TF32, products x1*y0 + x0*y1 + x0*y0.
+template <> struct Form<CHEB_TF32X3> {
+    static constexpr int SA = 2, SB = 2, NPROD = 3, EBYTES = 4, FMT = 2;
+    __device__ static constexpr int pa(int p) { return p == 0 ? 1 : 0; }
+    __device__ static constexpr int pb(int p) { return p == 1 ? 1 : 0; }
+};
+
+struct Params {
+    const void *X;
+    const double *B;
+    float *out;
+    int64_t R;
+    int n, m;
+    int Kp;        // K padded to the instruction K
+    int Np;        // N = m padded to 16
+    int tmem_cols; // power of two >= max(32, Np)
+    int *err;
+};
+
+__host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Split 16 bytes worth of consecutive K elements (8 BF16 / 4 TF32) of one
+// row into S parts (FP32 arithmetic) and store each part's 16-byte chunk.
+template <int FORM, int S>
+__device__ __forceinline__ void split_store_chunk(const float (&v)[16 / Form<FORM>::EBYTES],
+                                                  uint8_t *dst, uint32_t split_stride)
+{
+    if constexpr (Form<FORM>::EBYTES == 2) {
+        uint32_t w[S][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float a = v[2 * p], b = v[2 * p + 1];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // .x = a (low half)
+                w[s][p] = *reinterpret_cast<const uint32_t *>(&h);
+                const float2 f = __bfloat1622float2(h);
+                a -= f.x;
+                b -= f.y;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4 *>(dst + s * split_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    } else {
+        uint32_t w[S][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float r = v[e];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                w[s][e] = tf32_rna(r);
+                r -= __uint_as_float(w[s][e]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4 *>(dst + s * split_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+}
+
+template <int FORM, typename XT>
+__global__ void __launch_bounds__(kThreads, 2)
+modeprod_tc_kernel(const Params P)
+{
+    using F = Form<FORM>;
+    constexpr int E = 16 / F::EBYTES;       // K elements per 16-byte chunk
+    constexpr int SA = F::SA, SB = F::SB;
+    const int n = P.n, m = P.m, Kp = P.Kp, Np = P.Np;
+    const int KC = Kp / E;                  // 16-byte chunks along K
+    const int ksteps = KC / 2;              // one MMA covers 32 bytes of K
+    const uint32_t a_split_bytes = (uint32_t)kTileM * Kp * F::EBYTES;
+    const uint32_t b_split_bytes = (uint32_t)Np * Kp * F::EBYTES;
+    const uint32_t stage_bytes = (uint32_t)round_up(kTileM * n * (int)sizeof(XT), 128);
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;                                   // SA x [128 x Kp]
+    uint8_t *sB = sA + SA * a_split_bytes;                // SB x [Np x Kp]
+    uint8_t *sX = sB + SB * b_split_bytes;                // 2 x staged X tile
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sX + 2 * stage_bytes);  // [0,1] loads, [2] mma
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (P.R + kTileM - 1) / kTileM;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, (uint32_t)P.tmem_cols);
+        tmem_relinquish();
+    }
+
+    // B splits, once per CTA: rows j < Np, chunks c < KC.
+    for (int t = tid; t < Np * KC; t += kThreads) {
+        const int j = t / KC, c = t - j * KC;
+        float v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = c * E + e;
+            v[e] = (j < m && k < n) ? (float)P.B[(int64_t)j * n + k] : 0.0f;
+        }
+        split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const XT *X = static_cast<const XT *>(P.X);
+    auto tile_full = [&](int64_t t) { return (t + 1) * kTileM <= P.R; };
+    auto issue_load = [&](int64_t t, int buf) {
+        const uint32_t bytes = (uint32_t)(kTileM * n * sizeof(XT));
+        mbar_arrive_expect_tx(&bars[buf], bytes);
+        bulk_g2s(sX + buf * stage_bytes, X + t * kTileM * (int64_t)n, bytes, &bars[buf]);
+    };
+
+    uint32_t load_phase = 0;     // bit b: parity of the next completion of load buffer b
+    uint32_t load_pending = 0;   // bit b: a copy into buffer b is in flight
+    uint32_t mma_phase = 0;
+    int64_t tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles && tile_full(tile)) issue_load(tile, 0);
+    if (tile < ntiles && tile_full(tile)) load_pending |= 1u;
+
+    const uint32_t idesc = make_idesc(F::FMT, kTileM, Np);
+    const int row = tid & (kTileM - 1);     // conversion: row of the tile
+    const int chalf = tid >> 7;             // conversion: chunk parity
+    const int quarter = warp & 3;           // epilogue: TMEM lane quarter
+    const int ehalf = warp >> 2;            // epilogue: column-chunk parity
+    int it = 0;
+    for (; tile < ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles && tile_full(next)) {
+            if (tid == 0) issue_load(next, buf ^ 1);
+            load_pending |= 1u << (buf ^ 1);
+        }
+        const int rows = (int)((P.R - tile * kTileM) < kTileM ? (P.R - tile * kTileM) : kTileM);
+        const XT *xs;
+        if (load_pending & (1u << buf)) {
+            if (!mbar_wait_bounded(&bars[buf], (load_phase >> buf) & 1u, P.err)) *abort_flag = 1;
+            load_phase ^= 1u << buf;
+            load_pending &= ~(1u << buf);
+            xs = reinterpret_cast<const XT *>(sX + buf * stage_bytes);
+        } else {
+            // ragged last tile: plain loads straight from global memory
+            xs = X + tile * kTileM * (int64_t)n;
+        }
+        // split row `row` of the tile into SA parts (zero beyond the data)
+        {
+            const bool valid = row < rows;
+            const XT *xr = xs + row * n;
+            for (int c = chalf; c < KC; c += 2) {
+                float v[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = c * E + e;
+                    v[e] = (valid && k < n) ? (float)xr[k] : 0.0f;
+                }
+                split_store_chunk<FORM, SA>(v, sA + (uint32_t)c * (kTileM * 16) + row * 16, a_split_bytes);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (*abort_flag) break;
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int p = 0; p < F::NPROD; ++p) {
+                const uint32_t ab = a0 + F::pa(p) * a_split_bytes;
+                const uint32_t bb = b0 + F::pb(p) * b_split_bytes;
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint64_t ad = make_sdesc(ab + ks * 2 * (kTileM * 16), kTileM * 16, 128);
+                    const uint64_t bd = make_sdesc(bb + ks * 2 * (Np * 16), Np * 16, 128);
+                    if constexpr (F::FMT == 2)
+                        mma_tf32(tmem, ad, bd, idesc, (p | ks) != 0);
+                    else
+                        mma_bf16(tmem, ad, bd, idesc, (p | ks) != 0);
+                }
+            }
+            mma_commit(&bars[2]);
+        }
+        if (!mbar_wait_bounded(&bars[2], mma_phase, P.err)) *abort_flag = 1;
+        mma_phase ^= 1;
+        tc_fence_after();
+        // epilogue: rows 32*quarter + lane, column chunks ehalf, ehalf + 2, ...
+        {
+            const int r = quarter * 32 + lane;
+            const bool valid = r < rows;
+            const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+            float *o = P.out + tile * kTileM + r;
+            for (int c0 = ehalf * 16; c0 < Np; c0 += 32) {
+                uint32_t v[16];
+                tmem_ld16(lane_addr + c0, v);
+                tmem_ld_wait();
+                if (valid) {
+                    float *oc = o + (int64_t)c0 * P.R;
+                    const int lim = m - c0;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        if (q < lim) *oc = __uint_as_float(v[q]);
+                        oc += P.R;
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (*abort_flag) break;
+    }
+    // drain copies still in flight (abort path), then free TMEM
+    for (int b = 0; b < 2; ++b)
+        if (load_pending & (1u << b)) mbar_wait_bounded(&bars[b], (load_phase >> b) & 1u, P.err);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)P.tmem_cols);
+}
+
+template <int FORM> constexpr int kAlignK = (Form<FORM>::EBYTES == 2) ? 16 : 8;
+
+template <int FORM, typename XT>
+cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
+{
+    using F = Form<FORM>;
+    Params P = P0;
+    P.Kp = round_up(P.n, kAlignK<FORM>);
+    P.Np = round_up(P.m, 16);
+    int cols = 32;
+    while (cols < P.Np) cols *= 2;
+    P.tmem_cols = cols;
+    const size_t a_bytes = (size_t)F::SA * kTileM * P.Kp * F::EBYTES;
+    const size_t b_bytes = (size_t)F::SB * P.Np * P.Kp * F::EBYTES;
+    const size_t stage = (size_t)round_up(kTileM * P.n * (int)sizeof(XT), 128);
+    const size_t smem = a_bytes + b_bytes + 2 * stage + 64;
+    if (smem > 227 * 1024) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: tile does not fit in shared memory");
+    auto kern = modeprod_tc_kernel<FORM, XT>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared));
+        attr_done = true;
+    }
+    // CTAs per SM from the shared-memory budget (the occupancy query reports
+    // one CTA here although two fit), capped by TMEM columns and threads.
+    int per_sm = (int)(228 * 1024 / (smem + 1024));
+    per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
+    while (per_sm > 1 && per_sm * P.tmem_cols > 512) --per_sm;
+    const int64_t ntiles = (P.R + kTileM - 1) / kTileM;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm);
+    ProfScope prof("modeprod_tc R=" + std::to_string(P.R) + " n=" + std::to_string(P.n) +
+                       " m=" + std::to_string(P.m) + (sizeof(XT) == 8 ? " x=f64" : " x=f32"),
+                   st);
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(P);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+}  // namespace
+
+cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
+                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st)
+{
+    if (R <= 0 || m <= 0) return CHEB_OK;
+    if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
+    if (m > 256) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
+    if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
+        return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
+    Params P{};
+    P.X = X;
+    P.B = B;
+    P.out = out;
+    P.R = R;
+    P.n = n;
+    P.m = m;
+    P.err = ctx->d_error;
+    const int sms = ctx->num_sms;
+    switch (prec) {
+    case CHEB_BF16X3:
+        return x_f64 ? launch<CHEB_BF16X3, double>(P, sms, st) : launch<CHEB_BF16X3, float>(P, sms, st);
+    case CHEB_BF16X6:
+        return x_f64 ? launch<CHEB_BF16X6, double>(P, sms, st) : launch<CHEB_BF16X6, float>(P, sms, st);
+    case CHEB_TF32X3:
+        return x_f64 ? launch<CHEB_TF32X3, double>(P, sms, st) : launch<CHEB_TF32X3, float>(P, sms, st);
+    default:
+        return fail(CHEB_EINVAL, "modeprod_tc: not a split precision");
+    }
+}
+
+}  // namespace cheb

@@ -1,0 +1,174 @@
+"""Parity of cheb_fit / cheb_eval_grid / cheb_eval_points (CUDA, through the C ABI)
+against the FP64 CPU oracle, on seeded inputs.
+
+Error measure: max |gpu - oracle| / max |oracle| (max-normalised).
+Tolerances: FP64 1e-12 relative. Split forms: the bound derived for the form,
+   d * u_form * kappa,  kappa = sum|c| / max|f|  (|T_l| <= 1 on [-1, 1]),
+with u_form the per-product relative error of the split (see split_bound), and
+at most 1e-6 for TF32x3 and BF16x6 on the d=4, n=33 tensor grid.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2307_04688_gb300 as cb
+from paper_2307_04688_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SPLITS = ["tf32x3", "bf16x3", "bf16x6"]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def lobatto(n):
+    return np.cos(np.pi * np.arange(n) / (n - 1))
+
+
+def err(gpu, ref):
+    g = gpu.double().cpu().numpy() if isinstance(gpu, torch.Tensor) else gpu
+    return float(np.abs(g - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def split_bound(prec, d, c, ref):
+    """d * u * kappa: u = per-product relative error of the split form.
+
+    bf16x3: |x - x0 - x1| <= 2^-18 |x|, dropped x1*y1 <= 2^-18: u = 3 * 2^-18
+    bf16x6: residual 2^-27, dropped terms i + j >= 3 about 2^-26: u = 2^-24
+    tf32x3: |x - x0 - x1| <= 2^-22 |x|, dropped x1*y1 <= 2^-22: u = 3 * 2^-22
+    plus FP32 accumulation and the FP32 intermediates, 4 * 2^-24 per mode.
+    """
+    u = {"bf16x3": 3 * 2.0 ** -18, "bf16x6": 2.0 ** -24, "tf32x3": 3 * 2.0 ** -22}[prec]
+    u += 4 * 2.0 ** -24
+    kappa = np.abs(c).sum() / np.abs(ref).max()
+    return d * u * kappa
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = I.small_fit_workload()
+    c = w["coeffs"]
+    a = lobatto(17)
+    G = O.eval_grid(c, [a, a])                      # nodal values (oracle)
+    return w, c, G
+
+
+def test_fit_small_workload(ctx, small):
+    w, c, G = small
+    coef = cb.cheb_fit(ctx, dev(G))
+    ref = O.fit_nd(G)
+    assert err(coef, ref) < 1e-13
+    assert err(coef, c) < 1e-13
+    # in place
+    g2 = dev(G)
+    cb.cheb_fit(ctx, g2, g2)
+    assert err(g2, ref) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64"] + SPLITS)
+def test_eval_grid_small_workload(ctx, small, prec):
+    w, c, G = small
+    coef = dev(O.fit_nd(G))
+    g = w["grid"][0]
+    ref = O.eval_grid(O.fit_nd(G), [g, g])
+    out = cb.cheb_eval_grid(ctx, coef, [dev(g), dev(g)], prec=prec)
+    e = err(out, ref)
+    if prec == "fp64":
+        assert e < 1e-13
+    else:
+        assert e < split_bound(prec, 2, c, ref), e
+
+
+@pytest.mark.parametrize("prec", ["fp64"] + SPLITS)
+def test_eval_points_small_workload(ctx, small, prec):
+    w, c, G = small
+    coefn = O.fit_nd(G)
+    P = w["points"]
+    ref = O.eval_points(coefn, P)
+    out = cb.cheb_eval_points(ctx, dev(coefn), dev(P), prec=prec)
+    e = err(out, ref)
+    if prec == "fp64":
+        assert e < 1e-13
+    else:
+        assert e < split_bound(prec, 2, c, ref), e
+
+
+@pytest.fixture(scope="module")
+def big():
+    w = I.tensor_grid_workload()
+    c = w["coeffs"]
+    O.set_threads(max(1, min(16, __import__("os").cpu_count() or 1)))
+    ref = O.eval_grid(c, w["grid"])                 # full 64^4 oracle grid
+    return w, c, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64"] + SPLITS)
+def test_tensor_grid_d4_n33(ctx, big, prec):
+    w, c, ref = big
+    xs = [dev(g) for g in w["grid"]]
+    out = cb.cheb_eval_grid(ctx, dev(c), xs, prec=prec)
+    torch.cuda.synchronize()
+    e = err(out, ref)
+    print(f"tensor grid d=4 n=33 64^4 {prec}: max-normalised error {e:.3e}")
+    if prec == "fp64":
+        assert e < 1e-12
+    else:
+        bound = split_bound(prec, 4, c, ref)
+        assert e < bound, (e, bound)
+        if prec in ("tf32x3", "bf16x6"):
+            assert e < 1e-6
+
+
+def test_fit_d4_n33(ctx, big):
+    w, c, _ = big
+    a = lobatto(33)
+    G = O.eval_grid(c, [a] * 4)
+    coef = cb.cheb_fit(ctx, dev(G))
+    assert err(coef, O.fit_nd(G)) < 1e-12
+    assert err(coef, c) < 1e-12
+
+
+@pytest.mark.parametrize("shape,m", [((5, 7, 3), (1, 130, 17)), ((2,), (300,)), ((9, 4), (129, 3)),
+                                     ((2, 3, 2, 3, 2, 3), (3, 2, 3, 2, 3, 2)), ((64, 2), (5, 64))])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+def test_ragged_and_degenerate_shapes(ctx, shape, m, prec):
+    rng = np.random.default_rng(sum(shape))
+    c = rng.standard_normal(shape)
+    d = len(shape)
+    a = rng.uniform(-2, 0, d)
+    b = a + rng.uniform(0.5, 3, d)
+    xs = [rng.uniform(a[s] - 0.1, b[s] + 0.1, m[s]) for s in range(d)]     # slightly outside too
+    ref = O.eval_grid(c, xs, a, b)
+    if prec != "fp64" and max(m) > 256:
+        with pytest.raises(cb.ChebError) as ei:
+            cb.cheb_eval_grid(ctx, dev(c), [dev(x) for x in xs], a, b, prec=prec)
+        assert ei.value.status == 7
+        return
+    out = cb.cheb_eval_grid(ctx, dev(c), [dev(x) for x in xs], a, b, prec=prec)
+    e = err(out, ref)
+    tol = 1e-12 if prec == "fp64" else 8 * split_bound(prec, d, c, ref)
+    assert e < tol, (e, tol)
+    G = O.eval_grid(c, [lobatto(k) for k in shape])
+    assert err(cb.cheb_fit(ctx, dev(G)), c) < 1e-12
+    P = np.stack([rng.uniform(a[s], b[s], 257) for s in range(d)], axis=1)
+    refp = O.eval_points(c, P, a, b)
+    outp = cb.cheb_eval_points(ctx, dev(c), dev(P), a, b, prec="fp64")
+    assert err(outp, refp) < 1e-12
+
+
+def test_empty_and_invalid_arguments(ctx):
+    c = dev(np.ones((3, 3)))
+    out = cb.cheb_eval_points(ctx, c, torch.zeros((0, 2), dtype=torch.float64, device="cuda"))
+    assert out.numel() == 0
+    L = cb.load()
+    import ctypes as C
+    n = (C.c_int32 * 2)(3, 3)
+    assert L.cheb_fit(ctx.handle, 0, n, C.c_void_p(c.data_ptr()), C.c_void_p(c.data_ptr()), None) == 1
+    n_bad = (C.c_int32 * 2)(3, 65)
+    assert L.cheb_fit(ctx.handle, 2, n_bad, C.c_void_p(c.data_ptr()), C.c_void_p(c.data_ptr()), None) == 1
+    with pytest.raises(cb.ChebError):
+        cb.cheb_eval_grid(ctx, c, [dev([0.0]), dev([0.0])], a=[1.0, 0.0], b=[0.0, 1.0])
+    ctx.device_status()
