@@ -104,6 +104,11 @@ cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const
 cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
                         int64_t R, int n, int m, cheb_precision prec, cudaStream_t st);
 
+// modeprod_tc without a context: `err` is the device error word to use and
+// `num_sms` the SM count of the current device.
+cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
+                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st);
+
 // Host-side DCT-I matrix of eq. (forcoef), cached per n on the context.
 cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out);
 

@@ -325,6 +325,34 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
 
 }  // namespace
 
+cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
+                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st)
+{
+    if (R <= 0 || m <= 0) return CHEB_OK;
+    if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
+    if (m > 256) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
+    if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
+        return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
+    Params P{};
+    P.X = X;
+    P.B = B;
+    P.out = out;
+    P.R = R;
+    P.n = n;
+    P.m = m;
+    P.err = err;
+    switch (prec) {
+    case CHEB_BF16X3:
+        return x_f64 ? launch<CHEB_BF16X3, double>(P, num_sms, st) : launch<CHEB_BF16X3, float>(P, num_sms, st);
+    case CHEB_BF16X6:
+        return x_f64 ? launch<CHEB_BF16X6, double>(P, num_sms, st) : launch<CHEB_BF16X6, float>(P, num_sms, st);
+    case CHEB_TF32X3:
+        return x_f64 ? launch<CHEB_TF32X3, double>(P, num_sms, st) : launch<CHEB_TF32X3, float>(P, num_sms, st);
+    default:
+        return fail(CHEB_EINVAL, "modeprod_tc: not a split precision");
+    }
+}
+
 cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
                         int64_t R, int n, int m, cheb_precision prec, cudaStream_t st)
 {
