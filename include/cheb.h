@@ -169,6 +169,35 @@ CHEB_API cheb_status cheb_eval_points(cheb_ctx *ctx, int d, const int32_t *n, co
                              const double *a, const double *b, int64_t P, const double *x,
                              void *out, cheb_precision prec, void *stream);
 
+/*
+ * cheb_eval_grid_noalloc - cheb_eval_grid for the split forms, without any
+ * allocation and without a context.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, for example inside a host framework that has
+ * reserved all device memory in its own pool, or on a latency-bound path
+ * where cudaMalloc/cudaFree would synchronise the device; a context
+ * (cheb_create) allocates as well, so none is taken.
+ *
+ * Same arithmetic and arguments as cheb_eval_grid with prec in {CHEB_TF32X3,
+ * CHEB_BF16X3, CHEB_BF16X6} and `out` a device float array of prod(m); works
+ * on the current device. Limits: 2 <= n[s] <= 64, 1 <= m[s] <= 256, the
+ * T matrices (8 * sum_s m[s] n[s] bytes) at most 1 MiB, and any two
+ * consecutive intermediates of the mode-product chain together at most 64 MiB
+ * of FP32; larger requests return CHEB_EINVAL with the size in the message.
+ * coeffs must be 16-byte aligned.
+ * Scratch: one fixed device array of 65 MiB inside the library (held by every
+ * GPU that loads it until the process exits). Its address is looked up the
+ * first time the call runs on a device; make that first call before any
+ * stream capture. All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. Bounded device waits that run
+ * out are recorded only in the array's own error word (not reported).
+ */
+CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, const double *coeffs,
+                                            const double *a, const double *b, const int32_t *m,
+                                            const double *const *x, float *out,
+                                            cheb_precision prec, void *stream);
+
 /* ------------------------------------------------------------------------
  * The J-player pollution game (Section 2, linear-quadratic specification,
  * time step h, Section 2.1):
