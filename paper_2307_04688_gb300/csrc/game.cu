@@ -1,11 +1,532 @@
-// Pollution-game solver (placeholder until the device iteration lands).
+// The Chebyshev collocation iteration for the J-player pollution game
+// (Section 2.1 Steps 0-4, Section 3.4), batched over independent instances.
+//
+// State per instance (device): coefficient tensors C (J x n^J, the caller's
+// V buffer), nodal controls u (the caller's u buffer) and nodal values Vn of
+// the current iterate, their successors u_new / Vn_new, and the next-state
+// reference coordinates X (J x n^J). One iteration is
+//   next_state  : X_l(j) = 2 (pbar_l + h g_l(pbar_j, u^[r](pbar_j))) / P_M - 1
+//   player      : for every player i and node j, V_i^[r] along the next states
+//                 is a Chebyshev series in the player's own coordinate (the
+//                 others are fixed at u^[r]); Newton on it gives u^[r+1]_i(j)
+//                 and V^[r+1]_i(j); |V^[r+1] - V^[r]| feeds the residual
+//   refit       : C = fit(Vn_new) in FP64 (eq. (forcoef) along every mode)
+//   commit      : u, Vn <- u_new, Vn_new; residual test, stall test, counters
+// with every kernel skipping instances that are done. Iterations are
+// enqueued in chunks captured once into a CUDA graph; the host only reads the
+// per-instance status between chunks.
+//
+// Two evaluation kernels exist: FP64 on the CUDA cores (player_f64_kernel)
+// and the split-precision tensor-core kernel (game_tc.cu). A device-side
+// mode flag per instance selects one of them each iteration, so the switch
+// from split to FP64 iterations (polish) needs no host round trip.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
 #include "cheb_internal.cuh"
+#include "game_internal.cuh"
+
+namespace cheb {
+namespace game {
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+// g_l(p, u) = (1/m) sum_{l' != l} K[l][l'] (p_l' - p_l) - c_l p_l + beta_l u_l
+__device__ __forceinline__ double dynamics(const GameDev &g, int l, const double *p, double ul)
+{
+    double coup = 0.0;
+    for (int t = 0; t < g.J; ++t)
+        if (t != l) coup += g.K[l * g.J + t] * (p[t] - p[l]);
+    return coup * g.minv - g.c[l] * p[l] + g.beta[l] * ul;
+}
+
+__global__ void next_state_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats)
+{
+    const GameDev g = insts[blockIdx.y];
+    if (stats[blockIdx.y].done) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.NP) return;
+    double xr[4], pb[4];
+    node_coords(g, j, xr, pb);
+    for (int l = 0; l < g.J; ++l) {
+        const double q = pb[l] + g.h * dynamics(g, l, pb, g.u[l * g.NP + j]);
+        g.X[l * g.NP + j] = 2.0 * q / g.P_M - 1.0;
+    }
+}
+
+// FP64 player update: one thread per (node, player). The series in the
+// player's own coordinate is w[k] = sum over the other modes of
+// C_i[..k..] prod_s T_{k_s}(x_s(j)), by nested contraction (last mode first).
+__global__ void __launch_bounds__(128)
+player_f64_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats)
+{
+    const int inst = blockIdx.z, i = blockIdx.y;
+    const GameDev &gref = insts[inst];
+    GameStat *st = &stats[inst];
+    if (st->done || st->mode != 0) return;
+    const GameDev g = gref;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.NP) return;
+    const int J = g.J, n = g.n, NP = g.NP;
+    double T[4][kGameNMax];
+    for (int s = 0; s < J; ++s) {
+        if (s == i) continue;
+        const double x = g.X[s * NP + j];
+        T[s][0] = 1.0;
+        if (n > 1) T[s][1] = x;
+        for (int k = 2; k < n; ++k) T[s][k] = 2.0 * x * T[s][k - 1] - T[s][k - 2];
+    }
+    // strides of the modes in C_i (row-major)
+    int stride[4];
+    stride[J - 1] = 1;
+    for (int s = J - 2; s >= 0; --s) stride[s] = stride[s + 1] * n;
+    int other[3], no = 0;
+    for (int s = 0; s < J; ++s)
+        if (s != i) other[no++] = s;
+    const double *C = g.C + (size_t)i * NP;
+    double w[kGameNMax];
+    for (int k = 0; k < n; ++k) {
+        const double *Ck = C + (size_t)k * stride[i];
+        double acc = 0.0;
+        if (no == 0) {
+            acc = Ck[0];
+        } else if (no == 1) {
+            const int s0 = other[0];
+            for (int a = 0; a < n; ++a) acc = fma(Ck[a * stride[s0]], T[s0][a], acc);
+        } else if (no == 2) {
+            const int s0 = other[0], s1 = other[1];
+            for (int a = 0; a < n; ++a) {
+                double t = 0.0;
+                const double *Ca = Ck + a * stride[s0];
+                for (int b = 0; b < n; ++b) t = fma(Ca[b * stride[s1]], T[s1][b], t);
+                acc = fma(t, T[s0][a], acc);
+            }
+        } else {
+            const int s0 = other[0], s1 = other[1], s2 = other[2];
+            for (int a = 0; a < n; ++a) {
+                double ta = 0.0;
+                for (int b = 0; b < n; ++b) {
+                    double t = 0.0;
+                    const double *Cab = Ck + a * stride[s0] + b * stride[s1];
+                    for (int c = 0; c < n; ++c) t = fma(Cab[c * stride[s2]], T[s2][c], t);
+                    ta = fma(t, T[s1][b], ta);
+                }
+                acc = fma(ta, T[s0][a], acc);
+            }
+        }
+        w[k] = acc;
+    }
+    player_finish(g, st, i, j, w);
+}
+
+// u, Vn <- u_new, Vn_new for instances still running (grid: node blocks x instances).
+__global__ void commit_copy_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats)
+{
+    if (stats[blockIdx.y].done) return;
+    const GameDev g = insts[blockIdx.y];
+    const int total = g.J * g.NP;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        g.u[t] = g.u_new[t];
+        g.Vn[t] = g.Vn_new[t];
+    }
+}
+
+// Residual test of Step 4 and the counters (one thread per instance).
+__global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B)
+{
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= B) return;
+    GameStat &s = stats[inst];
+    if (s.done) return;
+    const GameDev &g = insts[inst];
+    const double res = __longlong_as_double((long long)s.res_bits);
+    s.res_bits = 0ull;
+    s.iters += 1;
+    if (s.mode == 1) s.iters_split += 1;
+    s.last_res = res;
+    if (res < s.best_res * 0.999) {
+        s.best_res = res;
+        s.since_best = 0;
+    } else {
+        s.since_best += 1;
+    }
+    if (res < g.tol) {
+        s.done = 1;
+        s.status = CHEB_OK;
+    } else if (s.iters >= g.max_iter) {
+        s.done = 1;
+        s.status = CHEB_ENOCONV;
+    } else if (s.since_best > g.stall_window) {
+        if (s.mode == 1 && g.polish) {
+            s.mode = 0;                 // continue in FP64
+            s.since_best = 0;
+            s.best_res = res;
+        } else {
+            s.done = 1;
+            s.status = CHEB_ESTALL;
+        }
+    }
+}
+
+// Transpose [rows x G] -> [G x rows] (the fit chain leaves the instance-player
+// index last; this puts it back in front).
+__global__ void transpose_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t rows, int G)
+{
+    __shared__ double tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int g0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k;
+        const int gg = g0 + threadIdx.x;
+        if (r < rows && gg < G) tile[k][threadIdx.x] = in[r * G + gg];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int gg = g0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < rows && gg < G) out[(int64_t)gg * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+__global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0, int has_u0)
+{
+    const GameDev g = insts[blockIdx.y];
+    const int total = g.J * g.NP;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        g.Vn_new[t] = (has_v0 && g.V0) ? g.V0[t] : 0.0;
+        g.Vn[t] = g.Vn_new[t];
+        g.u[t] = (has_u0 && g.u0) ? g.u0[t] : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+// FP64 refit of every instance's Vn_new into C: the instances of a group are
+// contiguous, so the J nodal tensors of all B instances form one
+// (B J, n, ..., n) array; J rotating mode products (eq. (forcoef) along each
+// player's mode) leave the layout (l_1..l_J, B J), and a transpose restores
+// (B J, l_1..l_J).
+static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const double *Vn_new_all,
+                               double *C_all, double *tmp0, double *tmp1, cudaStream_t st)
+{
+    const int64_t total = (int64_t)G * NP;
+    const double *M = nullptr;
+    cheb_status r = dct_matrix(ctx, n, &M);
+    if (r) return r;
+    const double *src = Vn_new_all;
+    double *bufs[2] = {tmp0, tmp1};
+    for (int t = 0; t < J; ++t) {
+        double *dst = bufs[t & 1];
+        if ((r = modeprod_f64(src, M, dst, total / n, n, n, st))) return r;
+        src = dst;
+    }
+    dim3 grid((unsigned)((NP + 31) / 32), (unsigned)((G + 31) / 32));
+    {
+        ProfScope prof("game_transpose", st);
+        transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, C_all, NP, G);
+    }
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std::vector<int> &members,
+                        const cheb_game_params *params, const cheb_game_opts *opts, cheb_game_result *res,
+                        cudaStream_t st)
+{
+    const int B = (int)members.size();
+    const size_t per = (size_t)J * NP;       // doubles per instance per array
+    // All arrays are contiguous across the group (instance-major) so that the
+    // refit sees one (B J, n, .., n) tensor.
+    const size_t arr = sizeof(double) * per * B;
+    const size_t tc_bytes = game_tc_workspace_bytes(J, n, NP, B, prec);
+    size_t bytes = 0;
+    auto rnd = [](size_t x) { return (x + 255) & ~size_t(255); };
+    bytes += 9 * rnd(arr) + rnd(sizeof(double) * 64) + rnd(sizeof(GameDev) * B) + rnd(sizeof(GameStat) * B) +
+             rnd(tc_bytes);
+    cheb_status r = ctx->game.reserve(bytes);
+    if (r) return r;
+    uint8_t *base = static_cast<uint8_t *>(ctx->game.ptr);
+    size_t off = 0;
+    auto take = [&](size_t nbytes) {
+        uint8_t *p = base + off;
+        off += rnd(nbytes);
+        return p;
+    };
+    double *C_all = reinterpret_cast<double *>(take(arr));
+    double *u_all = reinterpret_cast<double *>(take(arr));
+    double *Vn_all = reinterpret_cast<double *>(take(arr));
+    double *u_new_all = reinterpret_cast<double *>(take(arr));
+    double *Vn_new_all = reinterpret_cast<double *>(take(arr));
+    double *X_all = reinterpret_cast<double *>(take(arr));
+    double *fit0 = reinterpret_cast<double *>(take(arr));
+    double *fit1 = reinterpret_cast<double *>(take(arr));
+    double *init = reinterpret_cast<double *>(take(arr));
+    double *nodes = reinterpret_cast<double *>(take(sizeof(double) * 64));
+    GameDev *d_inst = reinterpret_cast<GameDev *>(take(sizeof(GameDev) * B));
+    GameStat *d_stat = reinterpret_cast<GameStat *>(take(sizeof(GameStat) * B));
+    uint8_t *tc_ws = take(tc_bytes);
+    (void)init;
+
+    // nodes cos(pi k / N) (the integer argument is exact)
+    std::vector<double> hn(n);
+    for (int k = 0; k < n; ++k) hn[k] = std::cos(M_PI * (double)k / (double)(n - 1));
+    CHEB_CUDA_TRY(cudaMemcpyAsync(nodes, hn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+
+    std::vector<GameDev> hinst(B);
+    std::vector<GameStat> hstat(B);
+    bool any_v0 = false, any_u0 = false;
+    int64_t max_iter = 0;
+    for (int q = 0; q < B; ++q) {
+        const int b = members[q];
+        const cheb_game_params &p = params[b];
+        const cheb_game_opts &o = opts[b];
+        GameDev &g = hinst[q];
+        std::memset(&g, 0, sizeof(g));
+        g.J = J;
+        g.n = n;
+        g.NP = NP;
+        for (int t = 0; t < J * J; ++t) g.K[t] = p.K[t];
+        g.minv = 1.0 / p.m;
+        for (int t = 0; t < J; ++t) {
+            g.A[t] = p.A[t];
+            g.beta[t] = p.beta[t];
+            g.phi[t] = p.phi[t];
+            g.c[t] = p.c[t];
+        }
+        g.h = o.h;
+        g.delta = 1.0 - p.rho * o.h;
+        g.P_M = o.P_M;
+        g.U_M = o.U_M;
+        g.tol = o.tol;
+        g.max_iter = o.max_iter;
+        g.polish = o.polish_fp64 != 0;
+        g.stall_window = 200;
+        g.C = C_all + per * q;
+        g.u = u_all + per * q;
+        g.Vn = Vn_all + per * q;
+        g.u_new = u_new_all + per * q;
+        g.Vn_new = Vn_new_all + per * q;
+        g.X = X_all + per * q;
+        g.nodes = nodes;
+        g.V0 = res[b].V0;
+        g.u0 = res[b].u0;
+        any_v0 |= res[b].V0 != nullptr;
+        any_u0 |= res[b].u0 != nullptr;
+        max_iter = std::max<int64_t>(max_iter, o.max_iter);
+        GameStat &s = hstat[q];
+        std::memset(&s, 0, sizeof(s));
+        s.best_res = INFINITY;
+        s.last_res = INFINITY;
+        s.mode = prec == CHEB_FP64 ? 0 : 1;
+        s.status = CHEB_ENOCONV;
+    }
+    game_tc_bind(hinst.data(), B, J, n, NP, prec, tc_ws);
+    CHEB_CUDA_TRY(cudaMemcpyAsync(d_inst, hinst.data(), sizeof(GameDev) * B, cudaMemcpyHostToDevice, st));
+    CHEB_CUDA_TRY(cudaMemcpyAsync(d_stat, hstat.data(), sizeof(GameStat) * B, cudaMemcpyHostToDevice, st));
+
+    // ---- Step 0: initial nodal values and controls, fit ----
+    const unsigned copy_blocks = (unsigned)std::min<int64_t>(((int64_t)per + 255) / 256, 256);
+    init_state_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, any_v0, any_u0);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, st))) return r;
+
+    // ---- one iteration ----
+    const unsigned node_blocks = (unsigned)((NP + 127) / 128);
+    auto enqueue_iteration = [&](cudaStream_t s) -> cheb_status {
+        cheb_status e;
+        {
+            ProfScope prof("game_next_state", s);
+            next_state_kernel<<<dim3(node_blocks, B), 128, 0, s>>>(d_inst, d_stat);
+        }
+        CHEB_CUDA_TRY(cudaGetLastError());
+        if (prec != CHEB_FP64) {
+            if ((e = game_tc_player(ctx, d_inst, d_stat, hinst.data(), B, J, n, NP, prec, tc_ws, s))) return e;
+        }
+        if (prec == CHEB_FP64 || hinst[0].polish) {
+            ProfScope prof("game_player_f64", s);
+            player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
+        }
+        CHEB_CUDA_TRY(cudaGetLastError());
+        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, s))) return e;
+        {
+            ProfScope prof("game_commit", s);
+            commit_copy_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);
+            commit_stat_kernel<<<(B + 127) / 128, 128, 0, s>>>(d_inst, d_stat, B);
+        }
+        CHEB_CUDA_TRY(cudaGetLastError());
+        return CHEB_OK;
+    };
+
+    // ---- chunks of iterations, captured once into a CUDA graph ----
+    const int chunk = (int)std::min<int64_t>(max_iter, 32);
+    const bool use_graph = !ctx->prof_on;
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+        cudaStream_t cs = nullptr;
+        CHEB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(ce, "cudaStreamBeginCapture");
+        }
+        for (int t = 0; t < chunk && r == CHEB_OK; ++t) r = enqueue_iteration(cs);
+        ce = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    GameStat *hs = nullptr;
+    CHEB_CUDA_TRY(cudaMallocHost(&hs, sizeof(GameStat) * B * 2));
+    cudaEvent_t ev[2];
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    auto launch_chunk = [&](int slot) -> cheb_status {
+        if (use_graph) {
+            CHEB_CUDA_TRY(cudaGraphLaunch(exec, st));
+        } else {
+            for (int t = 0; t < chunk; ++t) {
+                cheb_status e = enqueue_iteration(st);
+                if (e) return e;
+            }
+        }
+        CHEB_CUDA_TRY(cudaMemcpyAsync(hs + slot * B, d_stat, sizeof(GameStat) * B, cudaMemcpyDeviceToHost, st));
+        CHEB_CUDA_TRY(cudaEventRecord(ev[slot], st));
+        return CHEB_OK;
+    };
+    // one chunk stays queued ahead of the one whose status is being read; every
+    // instance is marked done at max_iter, so at most max_iter / chunk + 2 chunks run
+    const int64_t max_chunks = max_iter / chunk + 2;
+    int64_t launched = 0;
+    int slot = 0;
+    r = launch_chunk(0);
+    ++launched;
+    while (r == CHEB_OK) {
+        bool queued_next = false;
+        if (launched < max_chunks) {
+            r = launch_chunk(slot ^ 1);
+            ++launched;
+            queued_next = true;
+            if (r) break;
+        }
+        cudaError_t ce = cudaEventSynchronize(ev[slot]);
+        if (ce != cudaSuccess) {
+            r = cuda_fail(ce, "game iteration");
+            break;
+        }
+        bool all_done = true;
+        for (int q = 0; q < B; ++q) all_done &= hs[slot * B + q].done != 0;
+        if (all_done || !queued_next) {
+            if (!all_done) {
+                r = fail(CHEB_ENOCONV, "game_solve: iteration budget exhausted");
+            }
+            break;
+        }
+        slot ^= 1;
+    }
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess && r == CHEB_OK) r = cuda_fail(ce, "game iteration");
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (r == CHEB_OK || r == CHEB_ENOCONV) {
+        // the status after the last chunk that ran (later chunks only skip)
+        CHEB_CUDA_TRY(cudaMemcpy(hs, d_stat, sizeof(GameStat) * B, cudaMemcpyDeviceToHost));
+        int err = 0;
+        CHEB_CUDA_TRY(cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < B; ++q) {
+            const int b = members[q];
+            const GameStat &s = hs[q];
+            res[b].iters = s.iters;
+            res[b].iters_split = s.iters_split;
+            res[b].residual = s.last_res;
+            res[b].status = s.done ? s.status : CHEB_ENOCONV;
+            if (err) res[b].status = err;
+            CHEB_CUDA_TRY(cudaMemcpyAsync(res[b].V, hinst[q].C, sizeof(double) * per, cudaMemcpyDeviceToDevice, st));
+            CHEB_CUDA_TRY(cudaMemcpyAsync(res[b].u, hinst[q].u, sizeof(double) * per, cudaMemcpyDeviceToDevice, st));
+        }
+        CHEB_CUDA_TRY(cudaStreamSynchronize(st));
+        r = CHEB_OK;
+    }
+    cudaFreeHost(hs);
+    return r;
+}
+
+}  // namespace game
+}  // namespace cheb
 
 using namespace cheb;
+using namespace cheb::game;
 
-extern "C" cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
-                                  const cheb_game_opts *opts, cheb_game_result *res, void *stream)
+extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
+                                           const cheb_game_opts *opts, cheb_game_result *res, void *stream)
 {
-    (void)ctx; (void)batch; (void)params; (void)opts; (void)res; (void)stream;
-    return fail(CHEB_EUNSUPPORTED, "game_solve: not built yet");
+    tl_ctx = ctx;
+    if (!ctx) return fail(CHEB_EINVAL, "null context");
+    if (batch < 1 || !params || !opts || !res) return fail(CHEB_EINVAL, "game_solve: bad batch or null arrays");
+    CHEB_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    struct Key {
+        int J, n, prec;
+        std::vector<int> members;
+    };
+    std::vector<Key> groups;
+    for (int b = 0; b < batch; ++b) {
+        const cheb_game_params &p = params[b];
+        const cheb_game_opts &o = opts[b];
+        if (p.J < 1 || p.J > 4) return fail(CHEB_EINVAL, "game_solve: J must be in [1, 4]");
+        if (o.n < 3 || o.n > kGameNMax) return fail(CHEB_EINVAL, "game_solve: n must be in [3, 33]");
+        if (o.n_u != 0 && o.n_u < o.n)
+            return fail(CHEB_EUNSUPPORTED, "game_solve: n_u must be 0 or >= n (exact control interpolant)");
+        if (!(o.h > 0) || !(p.rho > 0) || !(p.rho * o.h < 1) || !(o.P_M > 0) || !(o.U_M > 0) || !(p.m > 0) ||
+            !(o.tol >= 0) || o.max_iter < 1)
+            return fail(CHEB_EINVAL,
+                        "game_solve: need h, rho, P_M, U_M, m > 0, rho h < 1, tol >= 0, max_iter >= 1");
+        if (o.prec < CHEB_FP64 || o.prec > CHEB_BF16X6) return fail(CHEB_EINVAL, "game_solve: bad precision");
+        if (o.prec != CHEB_FP64 && (p.J != 3 || (o.n != 5 && o.n != 9 && o.n != 17 && o.n != 33)))
+            return fail(CHEB_EUNSUPPORTED, "game_solve: the split forms need J = 3 and n in {5, 9, 17, 33}");
+        for (int t = 0; t < p.J * p.J; ++t)
+            if (!std::isfinite(p.K[t])) return fail(CHEB_EINVAL, "game_solve: K not finite");
+        for (int t = 0; t < p.J; ++t)
+            if (!std::isfinite(p.A[t]) || !std::isfinite(p.beta[t]) || !std::isfinite(p.phi[t]) ||
+                !std::isfinite(p.c[t]) || !(p.phi[t] >= 0))
+                return fail(CHEB_EINVAL, "game_solve: parameters must be finite, phi >= 0");
+        if (!res[b].V || !res[b].u || res[b].V == res[b].u)
+            return fail(CHEB_EINVAL, "game_solve: V and u must be distinct device buffers");
+        res[b].status = CHEB_ENOCONV;
+        res[b].iters = 0;
+        res[b].iters_split = 0;
+        bool found = false;
+        for (auto &g : groups)
+            if (g.J == p.J && g.n == o.n && g.prec == o.prec) {
+                g.members.push_back(b);
+                found = true;
+                break;
+            }
+        if (!found) groups.push_back({p.J, o.n, o.prec, {b}});
+    }
+    for (auto &g : groups) {
+        int NP = 1;
+        for (int t = 0; t < g.J; ++t) NP *= g.n;
+        cheb_status r = solve_group(ctx, g.J, g.n, NP, g.prec, g.members, params, opts, res, st);
+        if (r) return r;
+    }
+    cheb_status first = CHEB_OK;
+    for (int b = 0; b < batch; ++b)
+        if (res[b].status != CHEB_OK && first == CHEB_OK) first = (cheb_status)res[b].status;
+    if (first != CHEB_OK) fail(first, "game_solve: an instance did not converge (see res[].status)");
+    return first;
 }

@@ -1,0 +1,149 @@
+// Shared declarations of the game solver (game.cu, game_tc.cu).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+namespace game {
+
+constexpr int kGameNMax = 33;     // nodes per player
+
+// One instance, device-resident (read-only during the iteration).
+struct GameDev {
+    int J, n, NP;                 // players, nodes per player, n^J
+    double K[16], minv;           // neighbour matrix, 1/m
+    double A[4], beta[4], phi[4], c[4];
+    double h, delta, P_M, U_M, tol;
+    long long max_iter;
+    int polish, stall_window;
+    double *C;                    // J x NP coefficient tensors of the current iterate
+    double *u, *Vn;               // nodal controls / values of the current iterate
+    double *u_new, *Vn_new;       // of the next iterate
+    double *X;                    // J x NP next-state reference coordinates
+    const double *nodes;          // cos(pi k / N), k < n
+    const double *V0, *u0;        // optional initial nodal values / controls
+    // split-precision path (game_tc.cu)
+    void *bsplit;                 // pre-split coefficient operands, J x chunks
+};
+
+// One instance's progress, written by the commit kernel.
+struct GameStat {
+    int done;
+    int mode;                     // 0: FP64 evaluation, 1: split precision
+    int status;                   // cheb_status once done
+    int since_best;
+    long long iters, iters_split;
+    unsigned long long res_bits;  // running max |dV| of this iteration (bits of a double >= 0)
+    double last_res, best_res;
+};
+
+// Node j: multi-index (j_0..j_{J-1}), last fastest; reference coordinate
+// cos(pi j_s / N), physical pbar_s = (P_M / 2)(x_s + 1) (Section 3.4, Step 0).
+__device__ __forceinline__ void node_coords(const GameDev &g, int j, double *xr, double *pb)
+{
+    int rem = j;
+    for (int s = g.J - 1; s >= 0; --s) {
+        const int k = rem % g.n;
+        rem /= g.n;
+        xr[s] = g.nodes[k];
+        pb[s] = 0.5 * g.P_M * (xr[s] + 1.0);
+    }
+}
+
+// W(u) = h (u (A - u/2) - phi pbar_i^2 / 2) + delta sum_m w_m T_m(xc + slope u)
+// (the Bellman objective of Section 2.1 along the next states, which are
+// affine in the player's own control) and its first two derivatives; T, T'
+// and T'' by differentiating the three-term recurrence, valid for any x.
+__device__ __forceinline__ void objective(const double *w, int n, double xc, double slope, double hA,
+                                          double hG0, double h, double delta, double u, double *W,
+                                          double *W1, double *W2)
+{
+    const double x = xc + slope * u;
+    double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0, e0 = 0.0, e1 = 0.0;
+    double s = w[0], s1 = 0.0, s2 = 0.0;
+    if (n > 1) {
+        s += w[1] * x;
+        s1 += w[1];
+    }
+    for (int m = 2; m < n; ++m) {
+        const double t2 = 2.0 * x * t1 - t0;
+        const double d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
+        const double e2 = 4.0 * d1 + 2.0 * x * e1 - e0;
+        s += w[m] * t2;
+        s1 += w[m] * d2;
+        s2 += w[m] * e2;
+        t0 = t1; t1 = t2;
+        d0 = d1; d1 = d2;
+        e0 = e1; e1 = e2;
+    }
+    *W = hA * u - 0.5 * h * u * u + hG0 + delta * s;
+    *W1 = hA - h * u + delta * slope * s1;
+    *W2 = -h + delta * slope * slope * s2;
+}
+
+// Step 3: the maximiser of W over [0, U_M]. Projected Newton from u0 (the
+// previous control; Section 3.4 recommends Newton), then the two bounds and
+// the Newton point compete: the largest W wins, ties to the smaller control.
+__device__ __forceinline__ double argmax_control(const double *w, int n, double xc, double slope, double hA,
+                                                 double hG0, double h, double delta, double U_M, double u0,
+                                                 double *Vbest)
+{
+    double u = fmin(fmax(u0, 0.0), U_M);
+    double W, W1, W2;
+    for (int it = 0; it < 30; ++it) {
+        objective(w, n, xc, slope, hA, hG0, h, delta, u, &W, &W1, &W2);
+        double un;
+        if (W2 < 0.0)
+            un = u - W1 / W2;
+        else
+            un = W1 > 0.0 ? 0.5 * (u + U_M) : 0.5 * u;   // not concave here: move towards ascent
+        un = fmin(fmax(un, 0.0), U_M);
+        const double step = fabs(un - u);
+        u = un;
+        if (step <= 1e-15 * U_M) break;
+    }
+    double best_u = 0.0, best_W;
+    objective(w, n, xc, slope, hA, hG0, h, delta, 0.0, &best_W, &W1, &W2);
+    objective(w, n, xc, slope, hA, hG0, h, delta, u, &W, &W1, &W2);
+    if (W > best_W) { best_W = W; best_u = u; }
+    objective(w, n, xc, slope, hA, hG0, h, delta, U_M, &W, &W1, &W2);
+    if (W > best_W) { best_W = W; best_u = U_M; }
+    *Vbest = best_W;
+    return best_u;
+}
+
+// Given the series w (player i's coordinate, node j), maximise, store the
+// new control and value, and fold |V_new - V_old| into the residual.
+__device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, int i, int j, const double *w)
+{
+    double xr[4], pb[4];
+    node_coords(g, j, xr, pb);
+    const int NP = g.NP;
+    const double ui = g.u[i * NP + j];
+    const double slope = 2.0 * g.h * g.beta[i] / g.P_M;           // dx_i / du_i
+    const double xc = g.X[i * NP + j] - slope * ui;
+    const double hA = g.h * g.A[i];
+    const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+    double V;
+    const double us = argmax_control(w, g.n, xc, slope, hA, hG0, g.h, g.delta, g.U_M, ui, &V);
+    g.u_new[i * NP + j] = us;
+    g.Vn_new[i * NP + j] = V;
+    const double d = fabs(V - g.Vn[i * NP + j]);
+    atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
+}
+
+cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std::vector<int> &members,
+                        const cheb_game_params *params, const cheb_game_opts *opts, cheb_game_result *res,
+                        cudaStream_t st);
+
+// ---- split-precision player update (game_tc.cu) ----
+size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec);
+void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws);
+cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, const GameDev *hinst, int B,
+                           int J, int n, int NP, int prec, uint8_t *ws, cudaStream_t st);
+
+}  // namespace game
+}  // namespace cheb

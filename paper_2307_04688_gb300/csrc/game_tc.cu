@@ -1,0 +1,541 @@
+// Split-precision player update of the game iteration on the tcgen05 tensor
+// cores (Section 3.4, Steps 1-3), J = 3 players.
+//
+// For player i with other modes a < b, node j and the next-state reference
+// coordinates x(j), V_i^[r] along the next states is the series
+//     w_j[k_i] = sum_{k_a, k_b} C_i[k_i, k_a, k_b] T_{k_a}(x_a(j)) T_{k_b}(x_b(j)),
+// a dense contraction: Y[j, (k_i, k_b)] = sum_{k_a} T_{k_a}(x_a(j)) C_i[k_i, k_a, k_b]
+// is a GEMM (M = nodes, K = n, N = n * n) and w_j[k_i] = sum_{k_b} Y[j, (k_i, k_b)] T_{k_b}(x_b(j))
+// is a row-wise reduction. One fused kernel does both for a 128-node tile:
+//  - the A operand T_{k_a}(x_a(j)) is formed in the kernel (double-float
+//    three-term recurrence, rounded to FP32, split into BF16/TF32 parts);
+//  - the B operand (C_i, columns (k_i, k_b) with k_b padded to a multiple of
+//    16) is split once per iteration by game_bprep_kernel into the canonical
+//    shared-memory layout, chunk by chunk (<= 256 columns), and each chunk is
+//    brought in by one bulk copy (TMA engine), double-buffered;
+//  - tcgen05.mma accumulates the split products of a chunk in TMEM (FP32);
+//  - the epilogue reads TMEM, multiplies by T_{k_b}(x_b(j)) (kept in
+//    registers) and writes w_j[k_i] to shared memory;
+//  - after the last chunk, one thread per node maximises over its control
+//    (Newton in FP32 from the previous control, the value at the maximiser in
+//    FP64) and writes the new control, value and the FP64 residual.
+#include <algorithm>
+#include <string>
+
+#include "game_internal.cuh"
+#include "tc_common.cuh"
+
+namespace cheb {
+namespace game {
+namespace {
+
+using namespace tc;
+
+constexpr int kTile = 128;
+constexpr int kThreads = 256;
+
+template <int FORM> struct GForm;
+template <> struct GForm<CHEB_BF16X3> {
+    static constexpr int SA = 2, SB = 2, NPROD = 3, EB = 2, FMT = 1, KALIGN = 16;
+    __device__ static constexpr int pa(int p) { return p == 0 ? 1 : 0; }
+    __device__ static constexpr int pb(int p) { return p == 1 ? 1 : 0; }
+};
+template <> struct GForm<CHEB_BF16X6> {
+    static constexpr int SA = 3, SB = 3, NPROD = 6, EB = 2, FMT = 1, KALIGN = 16;
+    __device__ static constexpr int pa(int p) { return p == 0 ? 2 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 1 : 0; }
+    __device__ static constexpr int pb(int p) { return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 2 : p == 3 ? 0 : p == 4 ? 1 : 0; }
+};
+template <> struct GForm<CHEB_TF32X3> {
+    static constexpr int SA = 2, SB = 2, NPROD = 3, EB = 4, FMT = 2, KALIGN = 8;
+    __device__ static constexpr int pa(int p) { return p == 0 ? 1 : 0; }
+    __device__ static constexpr int pb(int p) { return p == 1 ? 1 : 0; }
+};
+
+template <int FORM, int NN> struct Shape {
+    using F = GForm<FORM>;
+    static constexpr int NBP = (NN + 15) / 16 * 16;                 // k_b padded
+    static constexpr int KP = (NN + F::KALIGN - 1) / F::KALIGN * F::KALIGN;   // k_a padded
+    static constexpr int E = 16 / F::EB;                            // K elements per 16 bytes
+    static constexpr int KC = KP / E;                               // 16-byte chunks along K
+    static constexpr int CHKI = 256 / NBP < NN ? 256 / NBP : NN;    // k_i per column chunk
+    static constexpr int NCH = (NN + CHKI - 1) / CHKI;              // column chunks
+    static constexpr int NC = CHKI * NBP;                           // columns of a stored chunk
+    static constexpr int SPLIT_BYTES = NC * KP * F::EB;             // one split part of a chunk
+    static constexpr int CHUNK_BYTES = F::SB * SPLIT_BYTES;
+    static constexpr int A_SPLIT = kTile * KP * F::EB;
+    static constexpr int TMEM_COLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
+    static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
+                                   (size_t)NN * kTile * sizeof(float) + 128;
+};
+
+// ---- helpers -------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_from_double(double x)
+{
+    ff r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+// 2 x t1 - t0 in double-float arithmetic (error-free products and sums)
+__device__ __forceinline__ ff ff_cheb_step(ff x2, ff t1, ff t0)
+{
+    float p = x2.hi * t1.hi;
+    float e = fmaf(x2.hi, t1.hi, -p);
+    e = fmaf(x2.hi, t1.lo, e);
+    e = fmaf(x2.lo, t1.hi, e);
+    // (p + e) - (t0.hi + t0.lo)
+    const float s = p - t0.hi;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (-t0.hi - bb);
+    float lo = err + e - t0.lo;
+    float hi = s + lo;
+    lo = lo - (hi - s);
+    return {hi, lo};
+}
+
+// T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
+// double-float (the plain FP32 recurrence loses up to k^2 ulp near |x| = 1).
+template <int NN>
+__device__ __forceinline__ void cheb_row_f32(double x, float (&T)[NN])
+{
+    const ff xf = ff_from_double(x);
+    const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
+    ff t0 = {1.0f, 0.0f}, t1 = xf;
+    T[0] = 1.0f;
+    if (NN > 1) T[1] = xf.hi + xf.lo;
+#pragma unroll
+    for (int k = 2; k < NN; ++k) {
+        const ff t2 = ff_cheb_step(x2, t1, t0);
+        T[k] = t2.hi + t2.lo;
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
+template <int FORM, int S>
+__device__ __forceinline__ void split_store16(const float *v, uint8_t *dst, uint32_t split_stride)
+{
+    if constexpr (GForm<FORM>::EB == 2) {
+        uint32_t w[S][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float a = v[2 * p], b = v[2 * p + 1];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                w[s][p] = *reinterpret_cast<const uint32_t *>(&h);
+                const float2 f = __bfloat1622float2(h);
+                a -= f.x;
+                b -= f.y;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4 *>(dst + s * split_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    } else {
+        uint32_t w[S][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float r = v[e];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                w[s][e] = tf32_rna(r);
+                r -= __uint_as_float(w[s][e]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4 *>(dst + s * split_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+}
+
+// the two other modes (a < b) of player i in a 3-player game
+__device__ __forceinline__ void other_modes(int i, int &a, int &b)
+{
+    a = (i == 0) ? 1 : 0;
+    b = (i == 2) ? 1 : 2;
+}
+
+// ---- B operand: split C_i once per iteration -----------------------------------
+// Thread per (instance, player, chunk, row of the chunk, 16-byte K chunk).
+template <int FORM, int NN>
+__global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats, int B)
+{
+    using S = Shape<FORM, NN>;
+    using F = GForm<FORM>;
+    const int per_item = S::NC * S::KC;
+    const int64_t total = (int64_t)B * 3 * S::NCH * per_item;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(t % per_item);
+        const int64_t it = t / per_item;
+        const int c = (int)(it % S::NCH);
+        const int i = (int)((it / S::NCH) % 3);
+        const int q = (int)(it / (S::NCH * 3));
+        if (stats[q].done || stats[q].mode != 1) continue;
+        const GameDev &g = insts[q];
+        const int row = e / S::KC, kc = e - row * S::KC;
+        const int kl = row / S::NBP, kb = row - kl * S::NBP;
+        const int ki = c * S::CHKI + kl;
+        int a, b;
+        other_modes(i, a, b);
+        const int si = i == 0 ? NN * NN : i == 1 ? NN : 1;
+        const int sa = a == 0 ? NN * NN : a == 1 ? NN : 1;
+        const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
+        const double *C = g.C + (size_t)i * g.NP;
+        float v[S::E];
+#pragma unroll
+        for (int k = 0; k < S::E; ++k) {
+            const int ka = kc * S::E + k;
+            v[k] = (ki < NN && kb < NN && ka < NN)
+                       ? (float)C[ki * si + ka * sa + kb * sb]
+                       : 0.0f;
+        }
+        uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + ((size_t)i * S::NCH + c) * S::CHUNK_BYTES +
+                       (size_t)kc * (S::NC * 16) + (size_t)row * 16;
+        split_store16<FORM, F::SB>(v, dst, S::SPLIT_BYTES);
+    }
+}
+
+// ---- the fused player kernel ----------------------------------------------------
+template <int NN>
+__device__ __forceinline__ void objective_f32(const float (&w)[NN], float xc, float slope, float hA, float h,
+                                              float delta, float u, float &W, float &W1, float &W2)
+{
+    const float x = xc + slope * u;
+    float t0 = 1.f, t1 = x, d0 = 0.f, d1 = 1.f, e0 = 0.f, e1 = 0.f;
+    float s = w[0] + w[1] * x, s1 = w[1], s2 = 0.f;
+#pragma unroll
+    for (int m = 2; m < NN; ++m) {
+        const float t2 = 2.f * x * t1 - t0;
+        const float d2 = 2.f * t1 + 2.f * x * d1 - d0;
+        const float e2 = 4.f * d1 + 2.f * x * e1 - e0;
+        s = fmaf(w[m], t2, s);
+        s1 = fmaf(w[m], d2, s1);
+        s2 = fmaf(w[m], e2, s2);
+        t0 = t1; t1 = t2;
+        d0 = d1; d1 = d2;
+        e0 = e1; e1 = e2;
+    }
+    W = hA * u - 0.5f * h * u * u + delta * s;
+    W1 = hA - h * u + delta * slope * s1;
+    W2 = -h + delta * slope * slope * s2;
+}
+
+template <int FORM, int NN>
+__global__ void __launch_bounds__(kThreads, 1)
+game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B, int *err)
+{
+    using S = Shape<FORM, NN>;
+    using F = GForm<FORM>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;                                         // SA x [128 x KP]
+    uint8_t *sB = sA + F::SA * S::A_SPLIT;                      // 2 stages x CHUNK_BYTES
+    float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(w_s + NN * kTile);   // [0,1] B loads, [2] mma
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, S::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int NP = NN * NN * NN;
+    const int tiles = (NP + kTile - 1) / kTile;
+    const int64_t items = (int64_t)B * 3 * tiles;
+    uint32_t ld_phase = 0, mma_phase = 0;   // bit s: parity of stage s / of the mma barrier
+    uint32_t pending = 0;                   // bit s: a copy into stage s is in flight
+
+    const int row = tid & (kTile - 1);
+    const int half = tid >> 7;
+    const int quarter = warp & 3, ehalf = warp >> 2;
+
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int t = (int)(item % tiles);
+        const int i = (int)((item / tiles) % 3);
+        const int q = (int)(item / (tiles * 3));
+        GameStat *st = &stats[q];
+        if (st->done || st->mode != 1) continue;     // uniform across the block
+        const GameDev &g = insts[q];
+        int a, b;
+        other_modes(i, a, b);
+        const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::NCH * S::CHUNK_BYTES;
+        if (tid == 0) {
+            for (int c = 0; c < 2 && c < S::NCH; ++c) {
+                mbar_arrive_expect_tx(&bars[c], S::CHUNK_BYTES);
+                bulk_g2s(sB + c * S::CHUNK_BYTES, bsrc + (size_t)c * S::CHUNK_BYTES, S::CHUNK_BYTES, &bars[c]);
+                pending |= 1u << c;
+            }
+        }
+        // A operand and the epilogue factor for this thread's row (node)
+        const int j = t * kTile + row;
+        const bool valid = j < NP;
+        float Tb[S::NBP];
+        {
+            float Ta[NN], Tbn[NN];
+            const double xa = valid ? g.X[a * NP + j] : 0.0;
+            const double xb = valid ? g.X[b * NP + j] : 0.0;
+            cheb_row_f32<NN>(xa, Ta);
+            cheb_row_f32<NN>(xb, Tbn);
+#pragma unroll
+            for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < NN) ? Tbn[k] : 0.0f;
+#pragma unroll
+            for (int kc = 0; kc < S::KC; ++kc) {
+                if ((kc & 1) != half) continue;
+                float v[S::E];
+#pragma unroll
+                for (int e = 0; e < S::E; ++e) {
+                    const int k = kc * S::E + e;
+                    v[e] = (valid && k < NN) ? Ta[k < NN ? k : 0] : 0.0f;
+                }
+                split_store16<FORM, F::SA>(v, sA + (uint32_t)kc * (kTile * 16) + row * 16, S::A_SPLIT);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        for (int c = 0; c < S::NCH; ++c) {
+            const int stage = c & 1;
+            const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
+            const int N = kis * S::NBP;
+            if (tid == 0) {
+                if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
+                ld_phase ^= 1u << stage;
+                pending &= ~(1u << stage);
+                const uint32_t idesc = make_idesc(F::FMT, kTile, N);
+                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
+#pragma unroll
+                for (int p = 0; p < F::NPROD; ++p) {
+                    const uint32_t ab = a0 + F::pa(p) * S::A_SPLIT;
+                    const uint32_t bb = b0 + F::pb(p) * S::SPLIT_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < S::KC / 2; ++ks) {
+                        const uint64_t ad = make_sdesc(ab + ks * 2 * (kTile * 16), kTile * 16, 128);
+                        const uint64_t bd = make_sdesc(bb + ks * 2 * (S::NC * 16), S::NC * 16, 128);
+                        if constexpr (F::FMT == 2)
+                            mma_tf32(tmem, ad, bd, idesc, (p | ks) != 0);
+                        else
+                            mma_bf16(tmem, ad, bd, idesc, (p | ks) != 0);
+                    }
+                }
+                mma_commit(&bars[2]);
+            }
+            if (!mbar_wait_bounded(&bars[2], mma_phase & 1u, err)) *abort_flag = 1;
+            mma_phase ^= 1u;
+            tc_fence_after();
+            // stage is free again: prefetch chunk c + 2 into it
+            if (tid == 0 && c + 2 < S::NCH) {
+                mbar_arrive_expect_tx(&bars[stage], S::CHUNK_BYTES);
+                bulk_g2s(sB + stage * S::CHUNK_BYTES, bsrc + (size_t)(c + 2) * S::CHUNK_BYTES, S::CHUNK_BYTES,
+                         &bars[stage]);
+                pending |= 1u << stage;
+            }
+            // epilogue: rows 32 quarter + lane, k_i of this chunk alternate between halves
+            {
+                const int r = quarter * 32 + lane;
+                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+                // r == row: the epilogue row of this thread is the row whose
+                // T_b it computed above
+                for (int kl = ehalf; kl < kis; kl += 2) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int g16 = 0; g16 < S::NBP / 16; ++g16) {
+                        uint32_t v[16];
+                        tmem_ld16(lane_addr + kl * S::NBP + g16 * 16, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) acc = fmaf(__uint_as_float(v[e]), Tb[g16 * 16 + e], acc);
+                    }
+                    w_s[(c * S::CHKI + kl) * kTile + r] = acc;
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (*abort_flag) break;
+        }
+        if (*abort_flag) break;
+        // Step 3 for each node of the tile: one thread per node
+        if (tid < kTile && valid) {
+            float w[NN];
+#pragma unroll
+            for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
+            double xr[4], pb[4];
+            node_coords(g, j, xr, pb);
+            const double ui = g.u[i * NP + j];
+            const double slope = 2.0 * g.h * g.beta[i] / g.P_M;
+            const double xc = g.X[i * NP + j] - slope * ui;
+            const double hA = g.h * g.A[i];
+            const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+            const float U_M = (float)g.U_M;
+            float u = fminf(fmaxf((float)ui, 0.0f), U_M);
+            float W, W1, W2;
+            for (int itn = 0; itn < 12; ++itn) {
+                objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+                float un = (W2 < 0.0f) ? u - W1 / W2 : (W1 > 0.0f ? 0.5f * (u + U_M) : 0.5f * u);
+                un = fminf(fmaxf(un, 0.0f), U_M);
+                const float step = fabsf(un - u);
+                u = un;
+                if (step <= 1e-7f * U_M) break;
+            }
+            // W in FP64 (value only) at a control
+            auto value64 = [&](double uu) {
+                const double x = xc + slope * uu;
+                double t0 = 1.0, t1 = x, s = (double)w[0] + (double)w[1] * x;
+                for (int m = 2; m < NN; ++m) {
+                    const double t2 = 2.0 * x * t1 - t0;
+                    s = fma((double)w[m], t2, s);
+                    t0 = t1;
+                    t1 = t2;
+                }
+                return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
+            };
+            objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+            double us = (double)u;
+            double V;
+            if (u > 0.0f && u < U_M && W2 < 0.0f) {
+                // a concave stationary point inside (0, U_M): the maximiser
+                V = value64(us);
+            } else {
+                // at a bound or not concave: the bounds and the Newton point
+                // compete in FP64 (differences of W near a bound are far below
+                // FP32 resolution), ties to the smaller control
+                double bu = 0.0, bv = value64(0.0);
+                const double vn = value64(us);
+                if (vn > bv) { bv = vn; bu = us; }
+                const double vm = value64(g.U_M);
+                if (vm > bv) { bv = vm; bu = g.U_M; }
+                us = bu;
+                V = bv;
+            }
+            g.u_new[i * NP + j] = us;
+            g.Vn_new[i * NP + j] = V;
+            const double d = fabs(V - g.Vn[i * NP + j]);
+            atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
+        }
+        __syncthreads();
+    }
+    // drain copies in flight (abort path), free TMEM
+    if (tid == 0)
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (pending & (1u << s2)) mbar_wait_bounded(&bars[s2], (ld_phase >> s2) & 1u, err);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+template <int FORM, int NN>
+cheb_status launch_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, cudaStream_t st)
+{
+    using S = Shape<FORM, NN>;
+    static_assert(S::SMEM <= 227 * 1024, "game player tile does not fit in shared memory");
+    {
+        const int64_t total = (int64_t)B * 3 * S::NCH * S::NC * S::KC;
+        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+        ProfScope prof("game_bprep n=" + std::to_string(NN), st);
+        game_bprep_kernel<FORM, NN><<<blocks, 256, 0, st>>>(d_inst, d_stat, B);
+        CHEB_CUDA_TRY(cudaGetLastError());
+    }
+    auto kern = game_player_tc_kernel<FORM, NN>;
+    static bool attr = false;
+    if (!attr) {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared));
+        attr = true;
+    }
+    const int tiles = (NN * NN * NN + kTile - 1) / kTile;
+    const int64_t items = (int64_t)B * 3 * tiles;
+    const int grid = (int)std::min<int64_t>(items, ctx->num_sms);
+    ProfScope prof("game_player_tc n=" + std::to_string(NN), st);
+    kern<<<grid, kThreads, S::SMEM, st>>>(d_inst, d_stat, B, ctx->d_error);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+template <int FORM>
+cheb_status dispatch_n(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, cudaStream_t st)
+{
+    switch (n) {
+    case 5: return launch_player<FORM, 5>(ctx, d_inst, d_stat, B, st);
+    case 9: return launch_player<FORM, 9>(ctx, d_inst, d_stat, B, st);
+    case 17: return launch_player<FORM, 17>(ctx, d_inst, d_stat, B, st);
+    case 33: return launch_player<FORM, 33>(ctx, d_inst, d_stat, B, st);
+    default: return fail(CHEB_EUNSUPPORTED, "game_solve: split precision supports n in {5, 9, 17, 33}");
+    }
+}
+
+template <int FORM, int NN> constexpr size_t chunk_bytes() { return Shape<FORM, NN>::CHUNK_BYTES; }
+template <int FORM, int NN> constexpr int nchunks() { return Shape<FORM, NN>::NCH; }
+
+size_t bsplit_bytes(int n, int prec)
+{
+#define CHEB_BS(FORM)                                                                   \
+    switch (n) {                                                                      \
+    case 5: return chunk_bytes<FORM, 5>() * nchunks<FORM, 5>();                       \
+    case 9: return chunk_bytes<FORM, 9>() * nchunks<FORM, 9>();                       \
+    case 17: return chunk_bytes<FORM, 17>() * nchunks<FORM, 17>();                    \
+    case 33: return chunk_bytes<FORM, 33>() * nchunks<FORM, 33>();                    \
+    default: return 0;                                                                \
+    }
+    switch (prec) {
+    case CHEB_BF16X3: CHEB_BS(CHEB_BF16X3)
+    case CHEB_BF16X6: CHEB_BS(CHEB_BF16X6)
+    case CHEB_TF32X3: CHEB_BS(CHEB_TF32X3)
+    default: return 0;
+    }
+#undef CHEB_BS
+}
+
+}  // namespace
+
+size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec)
+{
+    (void)NP;
+    if (prec == CHEB_FP64 || J != 3) return 0;
+    return (size_t)B * 3 * ((bsplit_bytes(n, prec) + 255) & ~size_t(255));
+}
+
+void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws)
+{
+    (void)NP;
+    if (prec == CHEB_FP64 || J != 3) return;
+    const size_t per = 3 * ((bsplit_bytes(n, prec) + 255) & ~size_t(255));
+    for (int q = 0; q < B; ++q) hinst[q].bsplit = ws + per * q;
+}
+
+cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, const GameDev *hinst, int B,
+                           int J, int n, int NP, int prec, uint8_t *ws, cudaStream_t st)
+{
+    (void)hinst;
+    (void)NP;
+    (void)ws;
+    if (J != 3) return fail(CHEB_EUNSUPPORTED, "game_solve: split precision needs J = 3");
+    switch (prec) {
+    case CHEB_BF16X3: return dispatch_n<CHEB_BF16X3>(ctx, d_inst, d_stat, B, n, st);
+    case CHEB_BF16X6: return dispatch_n<CHEB_BF16X6>(ctx, d_inst, d_stat, B, n, st);
+    case CHEB_TF32X3: return dispatch_n<CHEB_TF32X3>(ctx, d_inst, d_stat, B, n, st);
+    default: return fail(CHEB_EINVAL, "game_solve: bad precision");
+    }
+}
+
+}  // namespace game
+}  // namespace cheb

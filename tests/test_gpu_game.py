@@ -1,0 +1,205 @@
+"""Parity of game_solve (CUDA, through the C ABI) with the FP64 CPU oracle.
+
+- iteration by iteration on small instances (J = 2, 3, 4; tol = 0, fixed
+  number of passes): coefficient tensors and nodal controls, 1e-12 relative;
+- full size n = 17, J = 3 (the +-30 % parameter draw, seed 2): the converged
+  FP64 solve against the closed-form LQ recursion run for the same number of
+  passes (valid while the control bounds stay inactive, which is checked),
+  and single node updates at sampled nodes against the oracle's Steps 1-3;
+- batches mixing instances and sizes;
+- the split forms: solve to the split form's own residual floor, then state
+  the error against the FP64 solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2307_04688_gb300 as cb
+from paper_2307_04688_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("J,n,R", [(3, 5, 1), (3, 5, 2), (3, 5, 7), (2, 5, 40), (4, 4, 5), (3, 9, 3),
+                                   (1, 6, 10)])
+def test_iterations_match_oracle(ctx, J, n, R):
+    p = I.draw_game_params(I.SplitMix64(10 + J * 7 + n), J)
+    o = cb.game_opts(n, tol=0.0, max_iter=R, prec="fp64")
+    V, u, res = cb.game_solve(ctx, p, o, raise_on_error=False)
+    assert res[0].iters == R
+    ref = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=R))
+    assert rel(V[0].cpu().numpy(), ref["Vcoef"]) < 1e-12
+    assert np.abs(u[0].cpu().numpy() - ref["u"]).max() < 1e-11
+    assert abs(res[0].residual - ref["residual"]) <= 1e-12 * max(ref["residual"], 1e-300) + 1e-17
+
+
+def test_kinked_domain_with_active_bound_matches_oracle(ctx):
+    """High damage, low benefit: u >= 0 binds at high pollution; V is only C^1 there."""
+    p = I.game_params(3, A=[0.2, 0.25, 0.2], phi=[3.0, 3.0, 3.0])
+    n, R = 7, 25
+    o = cb.game_opts(n, tol=0.0, max_iter=R, prec="fp64")
+    V, u, res = cb.game_solve(ctx, p, o, raise_on_error=False)
+    ref = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=R))
+    assert (ref["u"] == 0.0).any()                      # the bound is active somewhere
+    assert rel(V[0].cpu().numpy(), ref["Vcoef"]) < 1e-11
+    assert np.abs(u[0].cpu().numpy() - ref["u"]).max() < 1e-10
+
+
+def lq_nodal(p, h, R, pb):
+    lq = O.game_lq(p, h, R)
+    J = pb.shape[1]
+    V = np.empty((J, pb.shape[0]))
+    U = np.empty((J, pb.shape[0]))
+    for i in range(J):
+        Q, b, a = lq["Q"][R - 1, i], lq["b"][R - 1, i], lq["a"][R - 1, i]
+        V[i] = 0.5 * np.einsum("nj,jk,nk->n", pb, Q, pb) + pb @ b + a
+        U[i] = pb @ lq["F"][R - 1, i] + lq["f"][R - 1, i]
+    return V, U
+
+
+@pytest.fixture(scope="module")
+def full_fp64(ctx):
+    p = I.single_game_workload()
+    o = cb.game_opts(17, tol=1e-10, max_iter=20000, prec="fp64")
+    V, u, res = cb.game_solve(ctx, p, o)
+    return p, V[0].cpu().numpy(), u[0].cpu().numpy(), res[0]
+
+
+def test_full_size_fp64_converges_to_lq_solution(full_fp64):
+    p, V, u, r = full_fp64
+    assert r.status == 0 and r.residual < 1e-10
+    opts = O.make_opts(17)
+    pb, xr = O.game_nodes(opts, 3)
+    Vlq, Ulq = lq_nodal(p, 1e-2, int(r.iters), pb)
+    assert (Ulq > 0).all() and (Ulq < 1).all()          # bounds inactive: the pin applies
+    # nodal values of the GPU coefficients, evaluated by the oracle at the nodes
+    a = np.cos(np.pi * np.arange(17) / 16)
+    Vn = np.stack([O.eval_grid(V[i].reshape(17, 17, 17), [a, a, a]).reshape(-1) for i in range(3)])
+    assert rel(Vn, Vlq) < 1e-11
+    assert np.abs(u - Ulq).max() < 1e-10
+
+
+def test_full_size_sampled_node_updates(ctx):
+    p = I.single_game_workload()
+    n, R = 17, 12
+    V1, u1, _ = cb.game_solve(ctx, p, cb.game_opts(n, tol=0.0, max_iter=R - 1), raise_on_error=False)
+    V2, u2, _ = cb.game_solve(ctx, p, cb.game_opts(n, tol=0.0, max_iter=R), raise_on_error=False)
+    C1, U1 = V1[0].cpu().numpy(), u1[0].cpu().numpy()
+    C2, U2 = V2[0].cpu().numpy(), u2[0].cpu().numpy()
+    opts = O.make_opts(n, tol=0.0, max_iter=R)
+    pb, xr = O.game_nodes(opts, 3)
+    rng = np.random.default_rng(0)
+    for j in rng.choice(n ** 3, 12, replace=False):
+        for i in range(3):
+            us, vs, inside, conc = O.game_node_update(p, opts, i, pb[j], U1[:, j], C1[i])
+            assert abs(us - U2[i, j]) < 1e-10
+            v_gpu = O.eval_direct(C2[i].reshape(n, n, n), xr[j])
+            assert abs(vs - v_gpu) < 1e-12 * max(1.0, abs(vs))
+
+
+def test_batch_of_mixed_instances(ctx):
+    rng = I.SplitMix64(77)
+    ps = [I.draw_game_params(rng, 3) for _ in range(4)]
+    ns = [5, 7, 5, 6]
+    R = 6
+    opts = [cb.game_opts(k, tol=0.0, max_iter=R) for k in ns]
+    V, u, res = cb.game_solve(ctx, ps, opts, raise_on_error=False)
+    for q in range(4):
+        ref = O.game_solve(ps[q], O.make_opts(ns[q], tol=0.0, max_iter=R))
+        assert res[q].iters == R
+        assert rel(V[q].cpu().numpy(), ref["Vcoef"]) < 1e-12
+
+
+def test_invalid_arguments(ctx):
+    p = I.single_game_workload()
+    with pytest.raises(cb.ChebError) as e:
+        cb.game_solve(ctx, p, cb.game_opts(2))
+    assert e.value.status == 1
+    with pytest.raises(cb.ChebError) as e:
+        cb.game_solve(ctx, p, cb.game_opts(5, n_u=3))
+    assert e.value.status == 7
+    bad = dict(p)
+    bad["rho"] = -1.0
+    with pytest.raises(cb.ChebError):
+        cb.game_solve(ctx, bad, cb.game_opts(5))
+
+
+SPLIT_FORMS = ["bf16x6", "tf32x3", "bf16x3"]
+# relative error of one split evaluation, as in the grid tests (u_form + FP32 terms)
+U_FORM = {"bf16x3": 3 * 2.0 ** -18, "bf16x6": 2.0 ** -24, "tf32x3": 3 * 2.0 ** -22}
+
+
+@pytest.mark.parametrize("prec", SPLIT_FORMS)
+@pytest.mark.parametrize("n", [5, 9])
+def test_split_iterations_close_to_oracle(ctx, prec, n):
+    """A few passes in split precision: each evaluation carries the form's relative error
+    (bound: passes * (u_form + 2^-20) * kappa, kappa = sum |w| / |V| <= 10 for these smooth V)."""
+    p = I.single_game_workload()
+    R = 6
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(n, tol=0.0, max_iter=R, prec=prec, polish_fp64=False),
+                              raise_on_error=False)
+    assert res[0].iters == R and res[0].iters_split == R
+    ref = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=R))
+    bound = R * (U_FORM[prec] + 2.0 ** -20) * 10
+    e = rel(V[0].cpu().numpy(), ref["Vcoef"])
+    print(f"split {prec} n={n} after {R} passes: coefficient error {e:.2e} (bound {bound:.1e})")
+    assert e < bound
+    assert np.abs(u[0].cpu().numpy() - ref["u"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x3"])
+def test_split_sampled_node_updates_n33(ctx, prec):
+    """n = 33 (35,937 nodes): one split pass from a given state against the oracle's Steps 1-3
+    at sampled nodes (the oracle computes one node at a time)."""
+    p = I.single_game_workload()
+    n, R = 33, 4
+    o1 = cb.game_opts(n, tol=0.0, max_iter=R - 1, prec=prec, polish_fp64=False)
+    o2 = cb.game_opts(n, tol=0.0, max_iter=R, prec=prec, polish_fp64=False)
+    V1, u1, _ = cb.game_solve(ctx, p, o1, raise_on_error=False)
+    V2, u2, _ = cb.game_solve(ctx, p, o2, raise_on_error=False)
+    C1, U1 = V1[0].cpu().numpy(), u1[0].cpu().numpy()
+    C2, U2 = V2[0].cpu().numpy(), u2[0].cpu().numpy()
+    opts = O.make_opts(n, tol=0.0, max_iter=R)
+    rng = np.random.default_rng(1)
+    js = rng.choice(n ** 3, 6, replace=False)
+    for j in js:
+        pb = np.empty(3)
+        xr = np.empty(3)
+        import ctypes
+        O.lib().orc_game_node(ctypes.byref(opts), 3, int(j), pb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              xr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        for i in range(3):
+            us, vs, inside, conc = O.game_node_update(p, opts, i, pb, U1[:, j], C1[i])
+            v_gpu = O.eval_direct(C2[i].reshape(n, n, n), xr)
+            assert abs(us - U2[i, j]) < 1e-5
+            assert abs(vs - v_gpu) < 50 * (U_FORM[prec] + 2.0 ** -20) * max(1.0, abs(vs))
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x3"])
+def test_split_full_solve_error_vs_fp64(ctx, full_fp64, prec):
+    """n = 17 to the split form's residual floor, then with FP64 polish to 1e-10."""
+    p, Vf, uf, rf = full_fp64
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(17, tol=1e-10, max_iter=20000, prec=prec,
+                                                    polish_fp64=False), raise_on_error=False)
+    r = res[0]
+    e = rel(V[0].cpu().numpy(), Vf)
+    print(f"split {prec} n=17: status {r.status} iters {r.iters} residual {r.residual:.2e} "
+          f"coefficient error vs FP64 solve {e:.2e}")
+    assert r.status in (0, 5)
+    # floor of the split iteration: a few times the per-pass FP32-operand error (~4e-8)
+    assert r.residual < 1e-6
+    assert e < 1e-5
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(17, tol=1e-10, max_iter=20000, prec=prec,
+                                                    polish_fp64=True), raise_on_error=False)
+    r = res[0]
+    e = rel(V[0].cpu().numpy(), Vf)
+    print(f"split {prec} + FP64 polish n=17: status {r.status} iters {r.iters} (split {r.iters_split}) "
+          f"residual {r.residual:.2e} error {e:.2e}")
+    assert r.status == 0 and r.residual < 1e-10
+    # both solves stop within tol / (1 - delta_h) ~ 2e-8 of the fixed point, from either side
+    assert e < 1e-6
