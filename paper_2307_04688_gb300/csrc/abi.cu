@@ -343,7 +343,9 @@ cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double 
         Ts[s] = T + toff;
         toff += (size_t)m[s] * n[s];
     }
-    if ((st = cheb_matrices(d, x, m, n, a, b, Ts.data(), sm))) return st;
+    if (prec == CHEB_FP64) {
+        if ((st = cheb_matrices(d, x, m, n, a, b, Ts.data(), sm))) return st;
+    }
     const void *src = coeffs;
     int64_t cur = total;
     for (int t = 0; t < d; ++t) {
@@ -354,8 +356,8 @@ cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double 
             st = modeprod_f64(static_cast<const double *>(src), Ts[mode], static_cast<double *>(dst), R,
                               n[mode], m[mode], sm);
         else
-            st = modeprod_tc(ctx, src, t == 0, Ts[mode], static_cast<float *>(dst), R, n[mode], m[mode],
-                             prec, sm);
+            st = modeprod_tc(ctx, src, t == 0, nullptr, static_cast<float *>(dst), R, n[mode], m[mode],
+                             prec, sm, x[mode], a[mode], b[mode]);
         if (st) return st;
         cur = R * m[mode];
         src = dst;

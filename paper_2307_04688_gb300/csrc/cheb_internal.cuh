@@ -101,13 +101,18 @@ cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const
 
 // The same product as modeprod_f64 on the tensor cores. X is FP64 when
 // x_f64 != 0 and FP32 otherwise; B is FP64 (split on the fly); out is FP32.
+// With B null, B[j][k] = T_k(x~_j) is formed in the kernel from the m points
+// xpts on [ta, tb]. Launched with programmatic stream serialization: the
+// prologue overlaps the previous kernel's tail.
 cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
-                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st);
+                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st,
+                        const double *xpts = nullptr, double ta = -1.0, double tb = 1.0);
 
 // modeprod_tc without a context: `err` is the device error word to use and
 // `num_sms` the SM count of the current device.
 cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
-                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st);
+                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st,
+                            const double *xpts = nullptr, double ta = -1.0, double tb = 1.0);
 
 // Host-side DCT-I matrix of eq. (forcoef), cached per n on the context.
 cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out);

@@ -66,7 +66,9 @@ template <> struct Form<CHEB_TF32X3> {
 
 struct Params {
     const void *X;
-    const double *B;
+    const double *B;          // m x n FP64, or null: then B[j][k] = T_k(x~_j) from xpts
+    const double *xpts;       // m points on [ta, tb] (used when B is null)
+    double ta, tb;
     float *out;
     int64_t R;
     int n, m;
@@ -155,17 +157,49 @@ modeprod_tc_kernel(const Params P)
         tmem_relinquish();
     }
 
-    // B splits, once per CTA: rows j < Np, chunks c < KC.
-    for (int t = tid; t < Np * KC; t += kThreads) {
-        const int j = t / KC, c = t - j * KC;
-        float v[E];
+    // B splits, once per CTA: rows j < Np, chunks c < KC. With xpts given,
+    // row j is T_0..T_{n-1} at x~_j = (2 x_j - ta - tb) / (tb - ta) by the
+    // three-term recurrence in FP64 (one row per thread, then split).
+    if (P.B) {
+        for (int t = tid; t < Np * KC; t += kThreads) {
+            const int j = t / KC, c = t - j * KC;
+            float v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = c * E + e;
-            v[e] = (j < m && k < n) ? (float)P.B[(int64_t)j * n + k] : 0.0f;
+            for (int e = 0; e < E; ++e) {
+                const int k = c * E + e;
+                v[e] = (j < m && k < n) ? (float)P.B[(int64_t)j * n + k] : 0.0f;
+            }
+            split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
         }
-        split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+    } else {
+        for (int j = tid; j < Np; j += kThreads) {
+            const double xr = j < m ? (2.0 * P.xpts[j] - (P.ta + P.tb)) / (P.tb - P.ta) : 0.0;
+            double t0 = 1.0, t1 = xr;
+            for (int c = 0; c < KC; ++c) {
+                float v[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = c * E + e;
+                    double tk;
+                    if (k == 0) {
+                        tk = 1.0;
+                    } else if (k == 1) {
+                        tk = xr;
+                    } else {
+                        tk = 2.0 * xr * t1 - t0;
+                        t0 = t1;
+                        t1 = tk;
+                    }
+                    v[e] = (j < m && k < n) ? (float)tk : 0.0f;
+                }
+                split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+            }
+        }
     }
+    // everything above is independent of the previous kernel in the stream;
+    // from here on X (its output) is read
+    griddep_launch_dependents();
+    griddep_wait();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -318,15 +352,25 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
     ProfScope prof("modeprod_tc R=" + std::to_string(P.R) + " n=" + std::to_string(P.n) +
                        " m=" + std::to_string(P.m) + (sizeof(XT) == 8 ? " x=f64" : " x=f32"),
                    st);
-    kern<<<(unsigned)grid, kThreads, smem, st>>>(P);
-    CHEB_CUDA_TRY(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CHEB_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, P));
     return CHEB_OK;
 }
 
 }  // namespace
 
 cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
-                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st)
+                            int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st,
+                            const double *xpts, double ta, double tb)
 {
     if (R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
@@ -334,8 +378,12 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
     if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
         return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
     Params P{};
+    if (!B && !xpts) return fail(CHEB_EINVAL, "modeprod_tc: need B or the points");
     P.X = X;
     P.B = B;
+    P.xpts = xpts;
+    P.ta = ta;
+    P.tb = tb;
     P.out = out;
     P.R = R;
     P.n = n;
@@ -354,7 +402,8 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
 }
 
 cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B, float *out,
-                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st)
+                        int64_t R, int n, int m, cheb_precision prec, cudaStream_t st,
+                        const double *xpts, double ta, double tb)
 {
     if (R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
@@ -362,8 +411,12 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
     if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
         return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
     Params P{};
+    if (!B && !xpts) return fail(CHEB_EINVAL, "modeprod_tc: need B or the points");
     P.X = X;
     P.B = B;
+    P.xpts = xpts;
+    P.ta = ta;
+    P.tb = tb;
     P.out = out;
     P.R = R;
     P.n = n;
