@@ -272,6 +272,48 @@ typedef struct {
 CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
                        const cheb_game_opts *opts, cheb_game_result *res, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (surrogate). The paper starts the iteration from "some
+ * given" V^[0] (Section 2.1, Step 0); here a multilayer perceptron
+ * n_in -> width (x depth, GELU) -> n_out maps the game parameters to the
+ * coefficient tensor of one player's value function. BF16 operands with FP32
+ * accumulation on the tensor cores, FP32 master weights, Adam (b1 = 0.9,
+ * b2 = 0.999, eps = 1e-8), mean-squared error on normalised targets.
+ * ------------------------------------------------------------------------ */
+typedef struct cheb_mlp cheb_mlp;
+
+/* Create a network on the context's device. Weights He-uniform from
+ * SplitMix64(seed), biases zero. 1 <= n_in, width <= 8192; 0 <= depth <= 16. */
+CHEB_API cheb_status surrogate_create(cheb_ctx *ctx, int32_t n_in, int32_t width, int32_t depth,
+                                      int32_t n_out, uint64_t seed, cheb_mlp **net);
+CHEB_API cheb_status surrogate_destroy(cheb_mlp *net);
+
+/* Copy the flat FP32 parameter vector out (get, host, *count floats) and/or in
+ * (set, host; also resets the Adam state). Layout: for each layer W (out x in,
+ * row-major) then b (out). *count receives the parameter count. */
+CHEB_API cheb_status surrogate_params(cheb_mlp *net, float *get, const float *set, int64_t *count);
+
+/* Loss and gradient of one batch without normalisation: X device B x n_in
+ * FP32, T device B x n_out FP32; *loss (host) = mean squared error; grad
+ * (device, parameter count floats, optional). Synchronous when loss != NULL. */
+CHEB_API cheb_status surrogate_loss_grad(cheb_ctx *ctx, cheb_mlp *net, const float *X, const float *T,
+                                         int32_t B, float *loss, float *grad, void *stream);
+
+/* Train on S samples: X device FP64 (row i at X + i * x_stride, n_in values),
+ * Y device FP64 targets (row stride y_stride, n_out values). Inputs and
+ * targets are normalised by their training-set mean and standard deviation
+ * (kept in the network). `epochs` passes of shuffled mini-batches of `batch`
+ * samples (the shuffle is driven by SplitMix64(seed)); loss_per_epoch (host,
+ * optional) receives the mean normalised loss of every epoch. Synchronous. */
+CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double *X, int64_t x_stride,
+                                     const double *Y, int64_t y_stride, int64_t S, int32_t epochs,
+                                     int32_t batch, float lr, uint64_t seed, float *loss_per_epoch,
+                                     void *stream);
+
+/* Predict P outputs (device FP64, row stride y_stride) from device FP64 inputs. */
+CHEB_API cheb_status surrogate_predict(cheb_ctx *ctx, cheb_mlp *net, const double *X, int64_t x_stride,
+                                       int64_t P, double *Y, int64_t y_stride, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

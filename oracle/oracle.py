@@ -322,3 +322,40 @@ def game_lq(p, h: float, R: int):
     f = np.empty((R, J))
     lib().orc_game_lq(C.byref(P), float(h), int(R), _p(Q), _p(b), _p(a), _p(F), _p(f))
     return {"Q": Q, "b": b, "a": a, "F": F, "f": f}
+
+
+# ---- surrogate network (FP64) ----------------------------------------------
+
+def mlp_param_count(dims) -> int:
+    return int(sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1)))
+
+
+def mlp_forward(dims, params, X) -> np.ndarray:
+    d = _ivec(dims)
+    p, x = _f64(params), _f64(X)
+    B = x.shape[0]
+    out = np.empty((B, dims[-1]))
+    lib().orc_mlp_forward(len(dims) - 1, d.ctypes.data_as(_ip), _p(p), B, _p(x), _p(out), None)
+    return out
+
+
+def mlp_loss_grad(dims, params, X, T):
+    d = _ivec(dims)
+    p, x, t = _f64(params), _f64(X), _f64(T)
+    g = np.empty_like(p)
+    loss = lib().orc_mlp_loss_grad(len(dims) - 1, d.ctypes.data_as(_ip), _p(p), x.shape[0], _p(x), _p(t),
+                                   _p(g), None)
+    return float(loss), g
+
+
+def gelu(z: float) -> float:
+    return float(lib().orc_gelu(float(z)))
+
+
+def gelu_grad(z: float) -> float:
+    return float(lib().orc_gelu_grad(float(z)))
+
+
+def adam_step(w, g, m, v, lr, b1, b2, eps, t):
+    """In place on w, m, v (float64 arrays)."""
+    lib().orc_adam_step(w.size, _p(w), _p(_f64(g)), _p(m), _p(v), lr, b1, b2, eps, t)

@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import (CHEB_BF16X3, CHEB_BF16X6, CHEB_FP64, CHEB_TF32X3, PRECISIONS, ChebError,
                    GameOpts, GameParams, GameResult, check, load)
 
-__all__ = ["Context", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
+__all__ = ["Context", "Surrogate", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
            "CHEB_FP64", "CHEB_TF32X3", "CHEB_BF16X3", "CHEB_BF16X6", "ChebError", "precision"]
 
 
@@ -211,3 +211,76 @@ def game_solve(ctx: Context, params, opts, V=None, u=None, V0=None, u0=None, str
     if raise_on_error and st not in (_lib.CHEB_OK,):
         check(st)
     return Vs, us, [R[i] for i in range(B)]
+
+
+class Surrogate:
+    """The warm-start network (surrogate_* entry points of include/cheb.h)."""
+
+    def __init__(self, ctx: Context, n_in: int, width: int, depth: int, n_out: int, seed: int = 0):
+        self.ctx = ctx
+        self._h = C.c_void_p()
+        check(load().surrogate_create(ctx.handle, n_in, width, depth, n_out, C.c_uint64(seed), C.byref(self._h)))
+        self.n_in, self.n_out = n_in, n_out
+
+    def close(self):
+        if self._h:
+            load().surrogate_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self) -> int:
+        n = C.c_int64()
+        check(load().surrogate_params(self._h, None, None, C.byref(n)))
+        return int(n.value)
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.param_count(), dtype=np.float32)
+        check(load().surrogate_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), None, None))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.param_count():
+            raise ValueError("wrong parameter count")
+        check(load().surrogate_params(self._h, None, p.ctypes.data_as(C.POINTER(C.c_float)), None))
+
+    def loss_grad(self, X, T, stream=None):
+        """Unnormalised MSE loss and gradient of a batch (X, T float32 CUDA tensors)."""
+        import torch
+        _need_cuda(X, torch.float32, "X")
+        _need_cuda(T, torch.float32, "T")
+        g = torch.empty(self.param_count(), dtype=torch.float32, device=X.device)
+        loss = C.c_float()
+        check(load().surrogate_loss_grad(self.ctx.handle, self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                         int(X.shape[0]), C.byref(loss), C.c_void_p(g.data_ptr()),
+                                         _stream_ptr(stream)))
+        return float(loss.value), g
+
+    def train(self, X, Y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, stream=None):
+        """X (S x n_in) and Y (S x n_out, any row stride) float64 CUDA tensors; returns the loss per epoch."""
+        import torch
+        if X.dtype != torch.float64 or Y.dtype != torch.float64 or not X.is_cuda or not Y.is_cuda:
+            raise TypeError("X and Y must be float64 CUDA tensors")
+        if X.stride(1) != 1 or Y.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+        losses = (C.c_float * max(epochs, 1))()
+        check(load().surrogate_train(self.ctx.handle, self._h, C.c_void_p(X.data_ptr()), X.stride(0),
+                                     C.c_void_p(Y.data_ptr()), Y.stride(0), int(X.shape[0]), int(epochs), int(batch),
+                                     float(lr), C.c_uint64(seed), losses, _stream_ptr(stream)))
+        return [float(v) for v in losses[:epochs]]
+
+    def predict(self, X, out=None, stream=None):
+        import torch
+        if X.dtype != torch.float64 or not X.is_cuda or X.stride(1) != 1:
+            raise TypeError("X must be a float64 CUDA tensor with contiguous rows")
+        P = int(X.shape[0])
+        if out is None:
+            out = torch.empty((P, self.n_out), dtype=torch.float64, device=X.device)
+        check(load().surrogate_predict(self.ctx.handle, self._h, C.c_void_p(X.data_ptr()), X.stride(0), P,
+                                       C.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)))
+        return out

@@ -63,7 +63,8 @@ template <int FORM, int NN> struct Shape {
     static constexpr int SPLIT_BYTES = NC * KP * F::EB;             // one split part of a chunk
     static constexpr int CHUNK_BYTES = F::SB * SPLIT_BYTES;
     static constexpr int A_SPLIT = kTile * KP * F::EB;
-    static constexpr int TMEM_COLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;   // one buffer
+    static constexpr int TMEM_ALLOC = 2 * TMEM_COLS;                // two accumulators (<= 512)
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) + 128;
 };
@@ -236,7 +237,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     uint8_t *sA = smem;                                         // SA x [128 x KP]
     uint8_t *sB = sA + F::SA * S::A_SPLIT;                      // 2 stages x CHUNK_BYTES
     float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(w_s + NN * kTile);   // [0,1] B loads, [2] mma
+    uint64_t *bars = reinterpret_cast<uint64_t *>(w_s + NN * kTile);   // [0,1] B loads, [2,3] mma per accumulator
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -245,11 +246,12 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init(&bars[2], 1);
+        mbar_init(&bars[3], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(tmem_slot, S::TMEM_COLS);
+        tmem_alloc(tmem_slot, S::TMEM_ALLOC);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -260,7 +262,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const int NP = NN * NN * NN;
     const int tiles = (NP + kTile - 1) / kTile;
     const int64_t items = (int64_t)B * 3 * tiles;
-    uint32_t ld_phase = 0, mma_phase = 0;   // bit s: parity of stage s / of the mma barrier
+    uint32_t ld_phase = 0, mma_phase = 0;   // bit s: parity of B stage s / of accumulator s
     uint32_t pending = 0;                   // bit s: a copy into stage s is in flight
 
     const int row = tid & (kTile - 1);
@@ -312,58 +314,65 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        for (int c = 0; c < S::NCH; ++c) {
+        // MMA of chunk c into accumulator c & 1 (thread 0); the accumulator of
+        // chunk c + 1 is filled while the epilogue drains chunk c
+        auto issue_mma = [&](int c) {
             const int stage = c & 1;
-            const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
+            const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
             const int N = kis * S::NBP;
-            if (tid == 0) {
-                if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
-                ld_phase ^= 1u << stage;
-                pending &= ~(1u << stage);
-                const uint32_t idesc = make_idesc(F::FMT, kTile, N);
-                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
-#pragma unroll
-                for (int p = 0; p < F::NPROD; ++p) {
-                    const uint32_t ab = a0 + F::pa(p) * S::A_SPLIT;
-                    const uint32_t bb = b0 + F::pb(p) * S::SPLIT_BYTES;
-#pragma unroll
-                    for (int ks = 0; ks < S::KC / 2; ++ks) {
-                        const uint64_t ad = make_sdesc(ab + ks * 2 * (kTile * 16), kTile * 16, 128);
-                        const uint64_t bd = make_sdesc(bb + ks * 2 * (S::NC * 16), S::NC * 16, 128);
-                        if constexpr (F::FMT == 2)
-                            mma_tf32(tmem, ad, bd, idesc, (p | ks) != 0);
-                        else
-                            mma_bf16(tmem, ad, bd, idesc, (p | ks) != 0);
-                    }
-                }
-                mma_commit(&bars[2]);
-            }
-            if (!mbar_wait_bounded(&bars[2], mma_phase & 1u, err)) *abort_flag = 1;
-            mma_phase ^= 1u;
+            if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
+            ld_phase ^= 1u << stage;
+            pending &= ~(1u << stage);
             tc_fence_after();
-            // stage is free again: prefetch chunk c + 2 into it
-            if (tid == 0 && c + 2 < S::NCH) {
-                mbar_arrive_expect_tx(&bars[stage], S::CHUNK_BYTES);
-                bulk_g2s(sB + stage * S::CHUNK_BYTES, bsrc + (size_t)(c + 2) * S::CHUNK_BYTES, S::CHUNK_BYTES,
-                         &bars[stage]);
-                pending |= 1u << stage;
+            const uint32_t idesc = make_idesc(F::FMT, kTile, N);
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
+            const uint32_t acc = tmem + (uint32_t)(stage * S::TMEM_COLS);
+#pragma unroll
+            for (int p = 0; p < F::NPROD; ++p) {
+                const uint32_t ab = a0 + F::pa(p) * S::A_SPLIT;
+                const uint32_t bb = b0 + F::pb(p) * S::SPLIT_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < S::KC / 2; ++ks) {
+                    const uint64_t ad = make_sdesc(ab + ks * 2 * (kTile * 16), kTile * 16, 128);
+                    const uint64_t bd = make_sdesc(bb + ks * 2 * (S::NC * 16), S::NC * 16, 128);
+                    if constexpr (F::FMT == 2)
+                        mma_tf32(acc, ad, bd, idesc, (p | ks) != 0);
+                    else
+                        mma_bf16(acc, ad, bd, idesc, (p | ks) != 0);
+                }
             }
-            // epilogue: rows 32 quarter + lane, k_i of this chunk alternate between halves
+            mma_commit(&bars[2 + stage]);
+        };
+        if (tid == 0) issue_mma(0);
+        for (int c = 0; c < S::NCH; ++c) {
+            const int buf = c & 1;
+            const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
+            if (tid == 0 && c + 1 < S::NCH) issue_mma(c + 1);
+            if (!mbar_wait_bounded(&bars[2 + buf], (mma_phase >> buf) & 1u, err)) *abort_flag = 1;
+            mma_phase ^= 1u << buf;
+            tc_fence_after();
+            // the B stage of chunk c is free again: prefetch chunk c + 2 into it
+            if (tid == 0 && c + 2 < S::NCH) {
+                mbar_arrive_expect_tx(&bars[buf], S::CHUNK_BYTES);
+                bulk_g2s(sB + buf * S::CHUNK_BYTES, bsrc + (size_t)(c + 2) * S::CHUNK_BYTES, S::CHUNK_BYTES,
+                         &bars[buf]);
+                pending |= 1u << buf;
+            }
+            // epilogue: rows 32 quarter + lane (the row whose T_b this thread
+            // holds), k_i of this chunk alternating between the two halves
             {
                 const int r = quarter * 32 + lane;
-                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-                // r == row: the epilogue row of this thread is the row whose
-                // T_b it computed above
+                const uint32_t lane_addr = tmem + (uint32_t)(buf * S::TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
                 for (int kl = ehalf; kl < kis; kl += 2) {
+                    uint32_t v[S::NBP / 16][16];
+#pragma unroll
+                    for (int g16 = 0; g16 < S::NBP / 16; ++g16) tmem_ld16(lane_addr + kl * S::NBP + g16 * 16, v[g16]);
+                    tmem_ld_wait();
                     float acc = 0.0f;
 #pragma unroll
-                    for (int g16 = 0; g16 < S::NBP / 16; ++g16) {
-                        uint32_t v[16];
-                        tmem_ld16(lane_addr + kl * S::NBP + g16 * 16, v);
-                        tmem_ld_wait();
+                    for (int g16 = 0; g16 < S::NBP / 16; ++g16)
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) acc = fmaf(__uint_as_float(v[e]), Tb[g16 * 16 + e], acc);
-                    }
+                        for (int e = 0; e < 16; ++e) acc = fmaf(__uint_as_float(v[g16][e]), Tb[g16 * 16 + e], acc);
                     w_s[(c * S::CHKI + kl) * kTile + r] = acc;
                 }
             }
@@ -395,16 +404,33 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 u = un;
                 if (step <= 1e-7f * U_M) break;
             }
-            // W in FP64 (value only) at a control
+            // W at a control: the series sum_m w_m T_m(x) in double-float
+            // (T by the recurrence in double-float, products and sums
+            // error-free), the rest in FP64
             auto value64 = [&](double uu) {
                 const double x = xc + slope * uu;
-                double t0 = 1.0, t1 = x, s = (double)w[0] + (double)w[1] * x;
+                const ff xf = ff_from_double(x);
+                const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
+                ff t0 = {1.0f, 0.0f}, t1 = xf;
+                double s = (double)w[0] + (double)w[1] * ((double)xf.hi + (double)xf.lo);
+                ff acc = {0.0f, 0.0f};
+#pragma unroll
                 for (int m = 2; m < NN; ++m) {
-                    const double t2 = 2.0 * x * t1 - t0;
-                    s = fma((double)w[m], t2, s);
+                    const ff t2 = ff_cheb_step(x2, t1, t0);
+                    // acc += w_m * t2 (error-free product, compensated sum)
+                    const float p = w[m] * t2.hi;
+                    float e = fmaf(w[m], t2.hi, -p);
+                    e = fmaf(w[m], t2.lo, e);
+                    const float sh = acc.hi + p;
+                    const float bb = sh - acc.hi;
+                    const float er = (acc.hi - (sh - bb)) + (p - bb);
+                    float lo = acc.lo + e + er;
+                    acc.hi = sh + lo;
+                    acc.lo = lo - (acc.hi - sh);
                     t0 = t1;
                     t1 = t2;
                 }
+                s += (double)acc.hi + (double)acc.lo;
                 return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
             };
             objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
@@ -439,7 +465,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tmem, S::TMEM_ALLOC);
 }
 
 template <int FORM, int NN>
