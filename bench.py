@@ -44,9 +44,12 @@ def parse():
     ap.add_argument("--form", default=HEADLINE_FORM)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-game", action="store_true", help="skip the game-solve measurements")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "surrogate"],
                     help="grid: the d=4 n=33 64^4 evaluation (default); batched: 1,024 uneven game solves")
     ap.add_argument("--count", type=int, default=1024, help="instances of the batched workload")
+    ap.add_argument("--train", type=int, default=20000, help="surrogate workload: training solves")
+    ap.add_argument("--test", type=int, default=2000, help="surrogate workload: held-out solves")
+    ap.add_argument("--epochs", type=int, default=60, help="surrogate workload: training epochs")
     return ap.parse_args()
 
 
@@ -471,12 +474,137 @@ def run_batched(args):
     ctx.close()
 
 
+def run_surrogate(args):
+    """Learned warm start for the 3-player game at n = 17: 20,000 + 2,000 parameter draws
+    (seed 3); method-generated training data (split solves to residual 1e-6); one
+    8 -> 4 x 256 -> 2 x 4,913 GELU network per player (BF16 on the tensor cores) predicting the
+    player's nodal values and nodal controls, whose fit is the coefficient tensor; warm-started
+    against cold-started solves of the held-out games (split form: all; FP64: a sample)."""
+    import torch
+    import paper_2307_04688_gb300 as cb
+    from paper_2307_04688_gb300 import build as B
+    from paper_2307_04688_gb300 import inputs as I
+    B.build()
+    ctx = cb.Context(0)
+    n, J = 17, 3
+    NP = n ** J
+    S, T = args.train, args.test
+    ps = I.surrogate_workload(seed=3, count=S + T)
+    X = torch.from_numpy(np.stack([I.game_param_vector(p) for p in ps])).cuda()
+    V = torch.empty((S + T, J, NP), dtype=torch.float64, device="cuda")
+    Vn = torch.empty((S + T, J, NP), dtype=torch.float64, device="cuda")
+    U = torch.empty((S + T, J, NP), dtype=torch.float64, device="cuda")
+    form = args.form
+    # 1. training data generated by the method itself
+    gen_opts = cb.game_opts(n, tol=1e-6, max_iter=20000, prec=form, polish_fp64=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, res = cb.game_solve(ctx, ps, [gen_opts] * (S + T), V=[V[q] for q in range(S + T)],
+                              u=[U[q] for q in range(S + T)], Vn=[Vn[q] for q in range(S + T)],
+                              raise_on_error=False)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    gen_iters = float(np.mean([r.iters for r in res]))
+    # targets per player: [nodal V_i | nodal u_i] (rows of 2 x 4,913)
+    Y = torch.empty((S + T, J, 2, NP), dtype=torch.float64, device="cuda")
+    Y[:, :, 0, :] = Vn
+    Y[:, :, 1, :] = U
+    del V, U
+    # 2. one network per player
+    nets, losses = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(J):
+        net = cb.Surrogate(ctx, X.shape[1], 256, 4, 2 * NP, seed=100 + i)
+        losses.append(net.train(X[:S], Y[:S, i].reshape(S, 2 * NP), epochs=args.epochs, batch=256, lr=1e-3, seed=i))
+        nets.append(net)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # 3. warm starts for the held-out games
+    Xt = X[S:].contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pred = torch.empty((T, J, 2, NP), dtype=torch.float64, device="cuda")
+    for i in range(J):
+        nets[i].predict(Xt, out=pred[:, i].reshape(T, 2 * NP))
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    # smooth the predicted values (fit, exponential filter, back to the nodes): node-to-node
+    # noise in V^[0] is amplified by the iteration near the clustered boundary nodes
+    V0 = []
+    for q in range(T):
+        v = pred[q, :, 0, :].contiguous()
+        for i in range(J):
+            cb.cheb_smooth(ctx, v[i].view(n, n, n), alpha=36.0, order=4)
+        V0.append(v)
+    u0 = [pred[q, :, 1, :].contiguous() for q in range(T)]
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    ref = Y[S:]
+    pred_err_V = float(((pred[:, :, 0] - ref[:, :, 0]).abs().amax(dim=(1, 2)) /
+                        ref[:, :, 0].abs().amax(dim=(1, 2))).median().item())
+    pred_err_u = float((pred[:, :, 1] - ref[:, :, 1]).abs().amax(dim=(1, 2)).median().item())
+    tps = ps[S:]
+
+    def solve(prec, warm, sub):
+        o = cb.game_opts(n, tol=1e-10, max_iter=20000, prec=prec, polish_fp64=(prec != "fp64"))
+        ps_ = [tps[q] for q in sub]
+        v0 = [V0[q] for q in sub] if warm else None
+        uu0 = [u0[q] for q in sub] if warm else None
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        Vs, _, rr = cb.game_solve(ctx, ps_, [o] * len(sub), V0=v0, u0=uu0, raise_on_error=False)
+        torch.cuda.synchronize()
+        return Vs, rr, time.perf_counter() - t1
+
+    every = list(range(T))
+    sample = list(range(0, T, max(1, T // 32)))[:32]
+    out = {}
+    for prec, sub in ((form, every), ("fp64", sample)):
+        Vc, rc, tc = solve(prec, False, sub)
+        Vw, rw, tw = solve(prec, True, sub)
+        ic = np.array([r.iters for r in rc])
+        iw = np.array([r.iters for r in rw])
+        out[prec] = {"instances": len(sub), "cold_iters_mean": float(ic.mean()), "warm_iters_mean": float(iw.mean()),
+                     "iters_saved_mean": float((ic - iw).mean()), "iters_saved_frac": float(1 - iw.sum() / ic.sum()),
+                     "cold_solves_per_s": len(sub) / tc,
+                     "warm_solves_per_s": len(sub) / (tw + t_pred * len(sub) / T),
+                     "status_ok": int(sum(r.status == 0 for r in rw)),
+                     "cold_restarts": int(sum(r.restarts for r in rw))}
+        if prec == "fp64":
+            fp64_cold = {q: Vc[k] for k, q in enumerate(sub)}
+            out[prec]["warm_vs_cold_coef_err_max"] = max(
+                float((Vw[k] - Vc[k]).abs().max() / Vc[k].abs().max()) for k in range(len(sub)))
+        else:
+            split_warm = {q: Vw[k] for k, q in enumerate(sub)}
+    errs = [float((split_warm[q] - fp64_cold[q]).abs().max() / fp64_cold[q].abs().max()) for q in sample]
+    line = {"metric": METRIC, "value": out[form]["warm_solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": 1e3 / out[form]["warm_solves_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": form + " + FP64 polish (games) / bf16 (network)",
+            "data": "synthetic (seed 3)",
+            "config": {"workload": f"learned warm start, 3-player game n=17, {S} training + {T} held-out draws",
+                       "network": "8 -> 4 x 256 (GELU) -> 2 x 4913 (nodal V_i, nodal u_i), one per player",
+                       "epochs": args.epochs},
+            "data_generation": {"seconds": t_gen, "iters_mean": gen_iters, "tol": 1e-6},
+            "training": {"seconds": t_train, "loss_first_last": [[l[0], l[-1]] for l in losses]},
+            "prediction": {"seconds": t_pred, "nodal_V_max_norm_err_median": pred_err_V,
+                           "nodal_u_max_err_median": pred_err_u},
+            "held_out": out,
+            "final_err_split_warm_vs_cold_fp64_max": max(errs)}
+    print(json.dumps(line))
+    for net in nets:
+        net.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

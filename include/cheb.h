@@ -126,6 +126,24 @@ CHEB_API cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const doub
                      double *coeffs, void *stream);
 
 /*
+ * cheb_filter - exponential spectral filter of a coefficient tensor, in place:
+ * p_l *= prod_s exp(-alpha (l_s / N_s)^(2 order)). Not in the paper: the
+ * standard filter of spectral methods (Vandeven 1991; Gottlieb & Hesthaven
+ * 2001), used to smooth a predicted warm start before the iteration (the
+ * iteration amplifies node-to-node noise in V^[0] near the clustered boundary
+ * nodes). alpha = 36 makes the top mode vanish to double precision.
+ *  d, n, coeffs  as in cheb_fit (device, modified in place)
+ *  alpha >= 0, 1 <= order <= 32
+ */
+CHEB_API cheb_status cheb_filter(cheb_ctx *ctx, int d, const int32_t *n, double *coeffs, double alpha,
+                                 int32_t order, void *stream);
+
+/* cheb_smooth - nodal values -> fit (cheb_fit) -> cheb_filter -> values at the
+ * same nodes, in place on `values` (device, prod(n) doubles). */
+CHEB_API cheb_status cheb_smooth(cheb_ctx *ctx, int d, const int32_t *n, double *values, double alpha,
+                                 int32_t order, void *stream);
+
+/*
  * cheb_eval_grid - evaluate an interpolant on a tensor grid of points.
  *
  * Section 3.2: D(j_1..j_d) = I_N F(b^1_{j_1}, ..., b^d_{j_d}), computed as d
@@ -239,11 +257,16 @@ typedef struct {
                            return (player-major, each tensor row-major) */
     double *u;          /* device, J x n^J: nodal controls u_i(pbar_j) on return */
     const double *V0;   /* device or NULL: initial NODAL values J x n^J (zero if NULL) */
-    const double *u0;   /* device or NULL: initial nodal controls J x n^J (zero if NULL) */
+    const double *u0;   /* device or NULL: initial nodal controls J x n^J (zero if NULL;
+                           clamped to [0, U_M]) */
     int64_t iters;      /* out: iterations performed */
     int64_t iters_split;/* out: of which in split precision */
     double residual;    /* out: last residual */
     int32_t status;     /* out: cheb_status of this instance */
+    double *Vn;         /* device or NULL: receives the nodal values V_i(pbar_j), J x n^J */
+    int32_t restarts;   /* out: cold restarts after a diverging warm start (V0/u0 given):
+                           a non-finite residual, or one 1000x above its best after 20
+                           iterations, resets the instance to V = 0, u = 0 */
 } cheb_game_result;
 
 /*

@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import (CHEB_BF16X3, CHEB_BF16X6, CHEB_FP64, CHEB_TF32X3, PRECISIONS, ChebError,
                    GameOpts, GameParams, GameResult, check, load)
 
-__all__ = ["Context", "Surrogate", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
+__all__ = ["Context", "Surrogate", "cheb_filter", "cheb_smooth", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
            "CHEB_FP64", "CHEB_TF32X3", "CHEB_BF16X3", "CHEB_BF16X6", "ChebError", "precision"]
 
 
@@ -109,6 +109,24 @@ def cheb_fit(ctx: Context, values, coeffs=None, stream=None):
     return coeffs
 
 
+def cheb_filter(ctx: Context, coeffs, alpha: float = 36.0, order: int = 4, stream=None):
+    """Exponential spectral filter of a float64 coefficient tensor, in place."""
+    import torch
+    _need_cuda(coeffs, torch.float64, "coeffs")
+    check(load().cheb_filter(ctx.handle, coeffs.dim(), _i32(coeffs.shape), C.c_void_p(coeffs.data_ptr()),
+                             float(alpha), int(order), _stream_ptr(stream)))
+    return coeffs
+
+
+def cheb_smooth(ctx: Context, values, alpha: float = 36.0, order: int = 4, stream=None):
+    """Nodal values -> fit -> spectral filter -> values at the same nodes, in place."""
+    import torch
+    _need_cuda(values, torch.float64, "values")
+    check(load().cheb_smooth(ctx.handle, values.dim(), _i32(values.shape), C.c_void_p(values.data_ptr()),
+                             float(alpha), int(order), _stream_ptr(stream)))
+    return values
+
+
 def cheb_eval_grid(ctx: Context, coeffs, xs, a=None, b=None, prec="fp64", out=None, stream=None):
     """Values of the interpolant on the tensor grid xs[0] x ... x xs[d-1]."""
     import torch
@@ -183,8 +201,9 @@ def game_opts(n: int, h: float = 1e-2, P_M: float = 1.0, U_M: float = 1.0, tol: 
 
 
 def game_solve(ctx: Context, params, opts, V=None, u=None, V0=None, u0=None, stream=None,
-               raise_on_error: bool = True):
-    """Solve len(params) games; returns (V list, u list, result structs)."""
+               raise_on_error: bool = True, Vn=None):
+    """Solve len(params) games; returns (V list, u list, result structs). V: coefficient
+    tensors, u: nodal controls; Vn (optional list of J x n^J tensors) receives nodal values."""
     import torch
     if isinstance(params, dict):
         params = [params]
@@ -207,6 +226,7 @@ def game_solve(ctx: Context, params, opts, V=None, u=None, V0=None, u0=None, str
         R[i].u = ui.data_ptr()
         R[i].V0 = None if V0 is None or V0[i] is None else V0[i].data_ptr()
         R[i].u0 = None if u0 is None or u0[i] is None else u0[i].data_ptr()
+        R[i].Vn = None if Vn is None or Vn[i] is None else Vn[i].data_ptr()
     st = load().game_solve(ctx.handle, B, P, O, R, _stream_ptr(stream))
     if raise_on_error and st not in (_lib.CHEB_OK,):
         check(st)

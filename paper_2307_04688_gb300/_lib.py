@@ -41,7 +41,7 @@ class GameOpts(C.Structure):
 class GameResult(C.Structure):
     _fields_ = [("V", C.c_void_p), ("u", C.c_void_p), ("V0", C.c_void_p), ("u0", C.c_void_p),
                 ("iters", C.c_int64), ("iters_split", C.c_int64), ("residual", C.c_double),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("Vn", C.c_void_p), ("restarts", C.c_int32)]
 
 
 _lib = None
@@ -67,6 +67,10 @@ def load():
     L.cheb_eval_points.argtypes = [vp, C.c_int, ip, vp, dp, dp, C.c_int64, vp, vp, C.c_int, vp]
     L.game_solve.argtypes = [vp, C.c_int32, C.POINTER(GameParams), C.POINTER(GameOpts),
                              C.POINTER(GameResult), vp]
+    L.cheb_filter.argtypes = [vp, C.c_int, ip, vp, C.c_double, C.c_int32, vp]
+    L.cheb_filter.restype = C.c_int
+    L.cheb_smooth.argtypes = [vp, C.c_int, ip, vp, C.c_double, C.c_int32, vp]
+    L.cheb_smooth.restype = C.c_int
     L.cheb_profile.argtypes = [vp, C.c_int]
     L.cheb_profile_count.argtypes = [vp]
     L.cheb_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_int64),

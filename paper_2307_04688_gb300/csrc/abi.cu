@@ -125,6 +125,35 @@ cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out)
     return CHEB_OK;
 }
 
+// Evaluation at the Lobatto nodes, E[k, l] = T_l(alpha^k) = cos(pi l k / N),
+// cached per n on the context (key -n).
+cheb_status node_eval_matrix(cheb_ctx *ctx, int n, const double **out)
+{
+    auto it = ctx->dct.find(-n);
+    if (it != ctx->dct.end()) {
+        *out = it->second;
+        return CHEB_OK;
+    }
+    const int N = n - 1;
+    std::vector<double> E((size_t)n * n);
+    for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) {
+            const long t = ((long)l * k) % (2L * N);
+            E[(size_t)k * n + l] = std::cos(M_PI * (double)t / (double)N);
+        }
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * E.size());
+    if (e != cudaSuccess) return fail(CHEB_ENOMEM, "node matrix allocation failed");
+    e = cudaMemcpy(d, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "node matrix upload");
+    }
+    ctx->dct[-n] = d;
+    *out = d;
+    return CHEB_OK;
+}
+
 namespace {
 
 cheb_status check_ctx(cheb_ctx *ctx)
@@ -290,6 +319,46 @@ cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *value
         if ((st = dct_matrix(ctx, n[mode], &M))) return st;
         double *dst = (t == d - 1) ? coeffs : static_cast<double *>(ctx->ws[t & 1].ptr);
         if ((st = modeprod_f64(src, M, dst, total / n[mode], n[mode], n[mode], s))) return st;
+        src = dst;
+    }
+    return CHEB_OK;
+}
+
+cheb_status cheb_filter(cheb_ctx *ctx, int d, const int32_t *n, double *coeffs, double alpha, int32_t order,
+                        void *stream)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    int64_t total = 0;
+    if ((st = check_shape(d, n, 64, &total))) return st;
+    if (!coeffs) return fail(CHEB_EINVAL, "null coeffs");
+    if (!(alpha >= 0) || order < 1 || order > 32) return fail(CHEB_EINVAL, "cheb_filter: need alpha >= 0, 1 <= order <= 32");
+    return spectral_filter(d, n, coeffs, alpha, order, static_cast<cudaStream_t>(stream));
+}
+
+cheb_status cheb_smooth(cheb_ctx *ctx, int d, const int32_t *n, double *values, double alpha, int32_t order,
+                        void *stream)
+{
+    cheb_status st = cheb_fit(ctx, d, n, values, values, stream);
+    if (st) return st;
+    if ((st = cheb_filter(ctx, d, n, values, alpha, order, stream))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t total = 1;
+    for (int t = 0; t < d; ++t) total *= n[t];
+    if ((st = ctx->ws[0].reserve(sizeof(double) * total))) return st;
+    if ((st = ctx->ws[1].reserve(sizeof(double) * total))) return st;
+    // back to the nodes: T_l(alpha^k) = cos(pi l k / N), one product per mode
+    const double *src = values;
+    for (int t = 0; t < d; ++t) {
+        const int mode = d - 1 - t;
+        const double *E = nullptr;
+        if ((st = node_eval_matrix(ctx, n[mode], &E))) return st;
+        double *dst = (t == d - 1) ? values : static_cast<double *>(ctx->ws[t & 1].ptr);
+        if (t == d - 1 && d == 1) {
+            CHEB_CUDA_TRY(cudaMemcpyAsync(ctx->ws[1].ptr, values, sizeof(double) * total, cudaMemcpyDeviceToDevice, s));
+            src = static_cast<const double *>(ctx->ws[1].ptr);
+        }
+        if ((st = modeprod_f64(src, E, dst, total / n[mode], n[mode], n[mode], s))) return st;
         src = dst;
     }
     return CHEB_OK;

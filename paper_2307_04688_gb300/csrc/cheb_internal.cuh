@@ -92,6 +92,9 @@ cheb_status eval_points_tc(cheb_ctx *ctx, int d, const int32_t *n, const double 
                            const double *a, const double *b, int64_t P, const double *x, float *out,
                            cheb_precision prec, cudaStream_t st);
 
+// c[k] *= prod_s exp(-alpha (k_s / N_s)^(2 order)), in place.
+cheb_status spectral_filter(int d, const int32_t *n, double *coeffs, double alpha, int order, cudaStream_t st);
+
 // FP64 point evaluation: out[j] = sum_l c_l prod_s T_{l_s}(x~_{j,s}).
 cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const double *a,
                             const double *b, int64_t P, const double *x, double *out,
@@ -113,6 +116,9 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
 cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
                             int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st,
                             const double *xpts = nullptr, double ta = -1.0, double tb = 1.0);
+
+// Evaluation at the Lobatto nodes E[k, l] = cos(pi l k / N), cached per n.
+cheb_status node_eval_matrix(cheb_ctx *ctx, int n, const double **out);
 
 // Host-side DCT-I matrix of eq. (forcoef), cached per n on the context.
 cheb_status dct_matrix(cheb_ctx *ctx, int n, const double **out);

@@ -109,6 +109,31 @@ __global__ void cheb_matrices_kernel(ModeMats M)
     }
 }
 
+struct FilterDims {
+    int d;
+    int n[6];
+    double alpha;
+    int order;
+};
+
+// c[k] *= prod_s exp(-alpha (k_s / N_s)^(2 order)) (exponential spectral filter)
+__global__ void filter_kernel(FilterDims D, double *__restrict__ c, int64_t total)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = t;
+        double e = 0.0;
+        for (int s = D.d - 1; s >= 0; --s) {
+            const int k = (int)(rem % D.n[s]);
+            rem /= D.n[s];
+            const double eta = D.n[s] > 1 ? (double)k / (double)(D.n[s] - 1) : 0.0;
+            double p = 1.0;
+            for (int q = 0; q < 2 * D.order; ++q) p *= eta;
+            e += p;
+        }
+        c[t] *= exp(-D.alpha * e);
+    }
+}
+
 struct PointDims {
     int d;
     int n[6];
@@ -243,6 +268,23 @@ cheb_status cheb_matrix(const double *x, int64_t stride, int64_t m, int n, doubl
     if (m <= 0) return CHEB_OK;
     ProfScope prof("cheb_matrix", st);
     cheb_matrix_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(x, stride, m, n, a, b, T);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+cheb_status spectral_filter(int d, const int32_t *n, double *coeffs, double alpha, int order, cudaStream_t st)
+{
+    FilterDims D{};
+    D.d = d;
+    int64_t total = 1;
+    for (int s = 0; s < d; ++s) {
+        D.n[s] = n[s];
+        total *= n[s];
+    }
+    D.alpha = alpha;
+    D.order = order;
+    ProfScope prof("spectral_filter", st);
+    filter_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(D, coeffs, total);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }

@@ -136,6 +136,21 @@ __global__ void commit_copy_kernel(const GameDev *__restrict__ insts, const Game
     }
 }
 
+// Cold restart of instances whose warm start diverged: V = 0, u = 0 (the
+// coefficients of V = 0 are 0), as at a cold Step 0.
+__global__ void restart_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats)
+{
+    if (stats[blockIdx.y].restart != 1) return;
+    const GameDev g = insts[blockIdx.y];
+    const int total = g.J * g.NP;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        g.u[t] = 0.0;
+        g.Vn[t] = 0.0;
+        g.Vn_new[t] = 0.0;
+        g.C[t] = 0.0;
+    }
+}
+
 // Residual test of Step 4 and the counters (one thread per instance).
 __global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B)
 {
@@ -146,6 +161,7 @@ __global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *
     const GameDev &g = insts[inst];
     const double res = __longlong_as_double((long long)s.res_bits);
     s.res_bits = 0ull;
+    if (s.restart == 1) s.restart = 0;          // this iteration ran from the cold state
     s.iters += 1;
     if (s.mode == 1) s.iters_split += 1;
     s.last_res = res;
@@ -154,6 +170,17 @@ __global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *
         s.since_best = 0;
     } else {
         s.since_best += 1;
+    }
+    // a warm start that diverges (non-finite residual, or a residual a thousand
+    // times above its best after 20 iterations) falls back to the cold start
+    if (s.warm && (!isfinite(res) || (s.iters > 20 && res > 1e3 * s.best_res))) {
+        s.warm = 0;
+        s.restart = 1;
+        s.restarts += 1;
+        s.best_res = INFINITY;
+        s.since_best = 0;
+        s.mode = s.mode_initial;
+        return;
     }
     if (res < g.tol) {
         s.done = 1;
@@ -200,7 +227,7 @@ __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0,
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         g.Vn_new[t] = (has_v0 && g.V0) ? g.V0[t] : 0.0;
         g.Vn[t] = g.Vn_new[t];
-        g.u[t] = (has_u0 && g.u0) ? g.u0[t] : 0.0;
+        g.u[t] = (has_u0 && g.u0) ? fmin(fmax(g.u0[t], 0.0), g.U_M) : 0.0;
     }
 }
 
@@ -325,6 +352,8 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         s.best_res = INFINITY;
         s.last_res = INFINITY;
         s.mode = prec == CHEB_FP64 ? 0 : 1;
+        s.mode_initial = s.mode;
+        s.warm = (res[b].V0 != nullptr || res[b].u0 != nullptr) ? 1 : 0;
         s.status = CHEB_ENOCONV;
     }
     game_tc_bind(hinst.data(), B, J, n, NP, prec, tc_ws);
@@ -341,6 +370,10 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     const unsigned node_blocks = (unsigned)((NP + 127) / 128);
     auto enqueue_iteration = [&](cudaStream_t s) -> cheb_status {
         cheb_status e;
+        if (any_v0 || any_u0) {
+            restart_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);
+            CHEB_CUDA_TRY(cudaGetLastError());
+        }
         {
             ProfScope prof("game_next_state", s);
             next_state_kernel<<<dim3(node_blocks, B), 128, 0, s>>>(d_inst, d_stat);
@@ -453,10 +486,13 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
             res[b].iters = s.iters;
             res[b].iters_split = s.iters_split;
             res[b].residual = s.last_res;
+            res[b].restarts = s.restarts;
             res[b].status = s.done ? s.status : CHEB_ENOCONV;
             if (err) res[b].status = err;
             CHEB_CUDA_TRY(cudaMemcpyAsync(res[b].V, hinst[q].C, sizeof(double) * per, cudaMemcpyDeviceToDevice, st));
             CHEB_CUDA_TRY(cudaMemcpyAsync(res[b].u, hinst[q].u, sizeof(double) * per, cudaMemcpyDeviceToDevice, st));
+            if (res[b].Vn)
+                CHEB_CUDA_TRY(cudaMemcpyAsync(res[b].Vn, hinst[q].Vn, sizeof(double) * per, cudaMemcpyDeviceToDevice, st));
         }
         CHEB_CUDA_TRY(cudaStreamSynchronize(st));
         r = CHEB_OK;

@@ -33,8 +33,12 @@ struct GameDev {
 struct GameStat {
     int done;
     int mode;                     // 0: FP64 evaluation, 1: split precision
+    int mode_initial;             // the mode a (re)start begins in
     int status;                   // cheb_status once done
     int since_best;
+    int warm;                     // started from given V0 / u0 (a divergence restarts cold)
+    int restart;                  // 1: reset to the cold start at the next iteration
+    int restarts;                 // cold restarts performed
     long long iters, iters_split;
     unsigned long long res_bits;  // running max |dV| of this iteration (bits of a double >= 0)
     double last_res, best_res;

@@ -255,15 +255,15 @@ __global__ void adam_kernel(int64_t nparam, float *__restrict__ w, const float *
     }
 }
 
-// out (FP64, row stride so) = Y * std + mean
+// out (FP64, row stride so) = Y / inv_std + mean (the inverse of the target normalisation)
 __global__ void denorm_kernel(const float *__restrict__ Y, int64_t P, int F, const float *__restrict__ mean,
-                              const float *__restrict__ std_, double *__restrict__ out, int64_t so)
+                              const float *__restrict__ inv_std, double *__restrict__ out, int64_t so)
 {
     const int64_t total = P * F;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = t / F;
         const int f = (int)(t % F);
-        out[p * so + f] = (double)Y[t] * (double)std_[f] + (double)mean[f];
+        out[p * so + f] = (double)Y[t] / (double)inv_std[f] + (double)mean[f];
     }
 }
 
@@ -611,7 +611,10 @@ CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double 
             if ((r = backward(ctx, net, B, st))) break;
             net->adam_t += 1;
             const float c1 = 1.0f - std::pow(b1, (float)net->adam_t), c2 = 1.0f - std::pow(b2, (float)net->adam_t);
-            adam_kernel<<<blocks_for(net->nparam), 256, 0, st>>>(net->nparam, net->w, net->grad, net->m, net->v, lr,
+            // cosine decay of the learning rate over the run
+            const double prog = (double)(e * steps + s) / (double)std::max<int64_t>(1, (int64_t)epochs * steps);
+            const float lr_t = (float)(0.5 * lr * (1.0 + std::cos(M_PI * prog)));
+            adam_kernel<<<blocks_for(net->nparam), 256, 0, st>>>(net->nparam, net->w, net->grad, net->m, net->v, lr_t,
                                                                 b1, b2, eps, c1, c2);
             cudaError_t ce = cudaGetLastError();
             if (ce != cudaSuccess) r = cuda_fail(ce, "surrogate_train");
@@ -644,7 +647,7 @@ CHEB_API cheb_status surrogate_predict(cheb_ctx *ctx, cheb_mlp *net, const doubl
         gather_norm_kernel<<<blocks_for((int64_t)nb * F), 256, 0, st>>>(X + p0 * x_stride, x_stride, nullptr, nb, F,
                                                                         net->x_mean, net->x_inv, net->X);
         if ((r = forward(ctx, net, nb, st))) return r;
-        denorm_kernel<<<blocks_for((int64_t)nb * O), 256, 0, st>>>(output(net, nb), nb, O, net->y_mean, net->y_std,
+        denorm_kernel<<<blocks_for((int64_t)nb * O), 256, 0, st>>>(output(net, nb), nb, O, net->y_mean, net->y_inv,
                                                                    Y + p0 * y_stride, y_stride);
         CHEB_CUDA_TRY(cudaGetLastError());
     }

@@ -203,3 +203,23 @@ def test_split_full_solve_error_vs_fp64(ctx, full_fp64, prec):
     assert r.status == 0 and r.residual < 1e-10
     # both solves stop within tol / (1 - delta_h) ~ 2e-8 of the fixed point, from either side
     assert e < 1e-6
+
+
+def test_diverging_warm_start_falls_back_to_cold(ctx):
+    """A warm start with large node-to-node noise diverges (the iteration amplifies it near the
+    clustered boundary nodes); the solver detects it, restarts cold and still converges."""
+    p = I.single_game_workload()
+    n, J = 17, 3
+    o = cb.game_opts(n, tol=1e-10, max_iter=20000, prec="fp64")
+    Vc, uc, rc = cb.game_solve(ctx, p, o)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    V0 = 0.05 * torch.randn((J, n ** J), generator=g, device="cuda", dtype=torch.float64)
+    Vw, uw, rw = cb.game_solve(ctx, p, o, V0=[V0], raise_on_error=False)
+    assert rw[0].restarts >= 1 and rw[0].status == 0
+    assert rel(Vw[0].cpu().numpy(), Vc[0].cpu().numpy()) < 1e-6
+    # a good warm start (the converged values) needs no restart and a single pass
+    Vn = torch.empty((J, n ** J), dtype=torch.float64, device="cuda")
+    cb.game_solve(ctx, p, o, Vn=[Vn])
+    Vg, ug, rg = cb.game_solve(ctx, p, o, V0=[Vn], u0=[uc[0]])
+    assert rg[0].restarts == 0 and rg[0].iters <= 2
