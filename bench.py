@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default="grid", choices=["grid", "batched", "surrogate"],
                     help="grid: the d=4 n=33 64^4 evaluation (default); batched: 1,024 uneven game solves")
     ap.add_argument("--count", type=int, default=1024, help="instances of the batched workload")
+    ap.add_argument("--fp64-sample", type=int, default=24,
+                    help="batched workload: bound-active instances checked against the FP64 GPU path")
     ap.add_argument("--train", type=int, default=20000, help="surrogate workload: training solves")
     ap.add_argument("--test", type=int, default=2000, help="surrogate workload: held-out solves")
     ap.add_argument("--epochs", type=int, default=60, help="surrogate workload: training epochs")
@@ -145,6 +147,23 @@ def dist_setup(n_gpus):
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return rank, world, local
+
+
+def shard(count, rank, world):
+    """Contiguous block of [0, count) owned by `rank` (sizes differ by at most one)."""
+    base, extra = divmod(count, world)
+    lo = rank * base + min(rank, extra)
+    return range(lo, lo + base + (1 if rank < extra else 0))
+
+
+def gather_lists(values, world):
+    """Concatenate a list of floats from every rank (host objects, no data-path collective)."""
+    if world == 1:
+        return list(values)
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, list(values))
+    return [v for part in out for v in part]
 
 
 def barrier(world):
@@ -412,35 +431,44 @@ def lq_fixed_point_nodal(p, n, h=1e-2, P_M=1.0, U_M=1.0, R=6000):
 
 def run_batched(args):
     """1,024 independent 3-player games, n drawn from {9, 17, 33} per instance with
-    parameters within +-30 % of nominal (seed 2), in one game_solve call (one CUDA-graph
-    sequence per size class), split precision with FP64 residuals. Accuracy: each instance's
-    nodal V against the oracle's closed-form LQ fixed point (instances whose LQ control
-    leaves (0, U_M) somewhere are counted apart)."""
+    parameters within +-30 % of nominal (seed 2), in one game_solve call per rank (one
+    CUDA-graph sequence per size class), split precision with FP64 residuals. Under torchrun
+    the instances are sharded across ranks (independent problems, no collective on the data
+    path). Accuracy: each instance's nodal V against the oracle's closed-form LQ fixed point
+    where no control bound is active, and against the FP64 GPU path (oracle-validated) on a
+    sample where one is."""
     import torch
     import oracle as O
     import paper_2307_04688_gb300 as cb
     from paper_2307_04688_gb300 import build as B
     from paper_2307_04688_gb300 import inputs as I
-    B.build()
-    O.build()
-    ctx = cb.Context(0)
-    inst = I.batched_game_workload(seed=2, count=args.count)
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+        O.build()
+    barrier(world)
+    ctx = cb.Context(local)
+    inst_all = I.batched_game_workload(seed=2, count=args.count)
+    mine = list(shard(len(inst_all), rank, world))
+    inst = [inst_all[q] for q in mine]
     params = [p for _, p in inst]
     ns = [n for n, _ in inst]
     form = args.form
     opts = [cb.game_opts(n, tol=1e-10, max_iter=20000, prec=form, polish_fp64=False) for n in ns]
-    # warm-up: one small instance per size (kernel attributes, workspaces)
-    for nn in sorted(set(ns)):
+    for nn in sorted(set(ns)):     # warm-up: kernel attributes, workspaces
         cb.game_solve(ctx, params[0], cb.game_opts(nn, tol=0.0, max_iter=2, prec=form, polish_fp64=False),
                       raise_on_error=False)
     torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
+    barrier(world)
+    with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         V, u, res = cb.game_solve(ctx, params, opts, raise_on_error=False)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+    el = max_over_ranks(el, world)
     clocks = clk.summary()
-    errs, errs_by_n, bound_active = [], {}, 0
+    errs, errs_by_n, bound_active = [], {}, []
     iters = {}
     for q in range(len(inst)):
         n = ns[q]
@@ -448,30 +476,51 @@ def run_batched(args):
         a = np.cos(np.pi * np.arange(n) / (n - 1))
         C = V[q].cpu().numpy()
         Vg = np.stack([O.eval_grid(C[i].reshape(n, n, n), [a, a, a]).reshape(-1) for i in range(3)])
-        e = float(np.abs(Vg - Vref).max() / np.abs(Vref).max())
         iters.setdefault(n, []).append(int(res[q].iters))
         if not inside:
-            bound_active += 1
+            bound_active.append(q)
             continue
+        e = float(np.abs(Vg - Vref).max() / np.abs(Vref).max())
         errs.append(e)
         errs_by_n.setdefault(n, []).append(e)
-    counts = {n: ns.count(n) for n in sorted(set(ns))}
-    line = {"metric": METRIC, "value": len(inst) / el, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": form + "->f32 (FP64 residual)", "data": "synthetic (seed 2)",
-            "config": {"workload": f"{len(inst)} 3-player games, n drawn from {{9,17,33}} ({counts}), "
-                                   "tol 1e-10, stop at the split residual floor",
-                       "form": form},
-            "iterations_mean_by_n": {n: float(np.mean(v)) for n, v in iters.items()},
-            "status_counts": {str(s_): sum(1 for r in res if r.status == s_) for s_ in set(r.status for r in res)},
-            "error_vs_oracle_lq_fixed_point": {
-                "p50": float(np.percentile(errs, 50)) if errs else None,
-                "p99": float(np.percentile(errs, 99)) if errs else None,
-                "by_n_p50": {n: float(np.percentile(v, 50)) for n, v in errs_by_n.items()},
-                "instances": len(errs), "bound_active_excluded": bound_active},
-            "clocks": clocks}
-    print(json.dumps(line))
+    # bound-active instances: against the FP64 GPU path on a small sample (n = 9 and 17)
+    sample = [q for q in bound_active if ns[q] in (9, 17)][:max(0, args.fp64_sample // world)]
+    errs_fp64 = []
+    if sample:
+        Vf, _, _ = cb.game_solve(ctx, [params[q] for q in sample],
+                                 [cb.game_opts(ns[q], tol=1e-10, max_iter=20000, prec="fp64") for q in sample],
+                                 raise_on_error=False)
+        for k, q in enumerate(sample):
+            errs_fp64.append(float((V[q] - Vf[k]).abs().max() / Vf[k].abs().max()))
+    errs = gather_lists(errs, world)
+    errs_fp64 = gather_lists(errs_fp64, world)
+    n_bound = int(sum(gather_lists([float(len(bound_active))], world)))
+    counts = {n: [n_ for n_, _ in inst_all].count(n) for n in sorted(set(n_ for n_, _ in inst_all))}
+    statuses = gather_lists([float(r.status) for r in res], world)
+    it_all = {n: gather_lists(v, world) for n, v in sorted(iters.items())}
+    if rank == 0:
+        line = {"metric": METRIC, "value": len(inst_all) / el, "unit": "solves/s", "n_gpus": world, "steps": 1,
+                "warmup": 1, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": form + "->f32 (FP64 residual)", "data": "synthetic (seed 2)",
+                "config": {"workload": f"{len(inst_all)} 3-player games, n drawn from {{9,17,33}} ({counts}), "
+                                       "tol 1e-10, stop at the split residual floor",
+                           "form": form, "parallelism": f"instances sharded x{world}" if world > 1 else "1 GPU"},
+                "iterations_mean_by_n": {n: float(np.mean(v)) for n, v in it_all.items()},
+                "status_counts": {str(int(s_)): statuses.count(s_) for s_ in sorted(set(statuses))},
+                "error_vs_oracle_lq_fixed_point": {
+                    "p50": float(np.percentile(errs, 50)) if errs else None,
+                    "p99": float(np.percentile(errs, 99)) if errs else None,
+                    "instances": len(errs), "bound_active_excluded": n_bound},
+                "error_vs_fp64_gpu_path_bound_active_sample": {
+                    "p50": float(np.percentile(errs_fp64, 50)) if errs_fp64 else None,
+                    "p99": float(np.percentile(errs_fp64, 99)) if errs_fp64 else None,
+                    "instances": len(errs_fp64)},
+                "clocks": clocks}
+        print(json.dumps(line))
     ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_surrogate(args):
