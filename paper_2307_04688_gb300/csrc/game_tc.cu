@@ -70,35 +70,6 @@ template <int FORM, int NN> struct Shape {
 };
 
 // ---- helpers -------------------------------------------------------------------
-struct ff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ ff ff_from_double(double x)
-{
-    ff r;
-    r.hi = (float)x;
-    r.lo = (float)(x - (double)r.hi);
-    return r;
-}
-
-// 2 x t1 - t0 in double-float arithmetic (error-free products and sums)
-__device__ __forceinline__ ff ff_cheb_step(ff x2, ff t1, ff t0)
-{
-    float p = x2.hi * t1.hi;
-    float e = fmaf(x2.hi, t1.hi, -p);
-    e = fmaf(x2.hi, t1.lo, e);
-    e = fmaf(x2.lo, t1.hi, e);
-    // (p + e) - (t0.hi + t0.lo)
-    const float s = p - t0.hi;
-    const float bb = s - p;
-    const float err = (p - (s - bb)) + (-t0.hi - bb);
-    float lo = err + e - t0.lo;
-    float hi = s + lo;
-    lo = lo - (hi - s);
-    return {hi, lo};
-}
-
 // T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
 // double-float (the plain FP32 recurrence loses up to k^2 ulp near |x| = 1).
 template <int NN>

@@ -258,5 +258,38 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t (&o)[S])
     }
 }
 
+// ---- double-float (an FP32 pair hi + lo) -------------------------------------
+// GB300 runs FP64 at a small fraction of its FP32 rate; values that need more
+// than FP32 precision but are only ever rounded to FP32 are carried as pairs.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_from_double(double x)
+{
+    ff r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+// 2 x t1 - t0 in double-float arithmetic (error-free products and sums)
+__device__ __forceinline__ ff ff_cheb_step(ff x2, ff t1, ff t0)
+{
+    float p = x2.hi * t1.hi;
+    float e = fmaf(x2.hi, t1.hi, -p);
+    e = fmaf(x2.hi, t1.lo, e);
+    e = fmaf(x2.lo, t1.hi, e);
+    // (p + e) - (t0.hi + t0.lo)
+    const float s = p - t0.hi;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (-t0.hi - bb);
+    float lo = err + e - t0.lo;
+    float hi = s + lo;
+    lo = lo - (hi - s);
+    return {hi, lo};
+}
+
 }  // namespace tc
+
 }  // namespace cheb

@@ -159,7 +159,7 @@ modeprod_tc_kernel(const Params P)
 
     // B splits, once per CTA: rows j < Np, chunks c < KC. With xpts given,
     // row j is T_0..T_{n-1} at x~_j = (2 x_j - ta - tb) / (tb - ta) by the
-    // three-term recurrence in FP64 (one row per thread, then split).
+    // three-term recurrence in double-float (one row per thread, then split).
     if (P.B) {
         for (int t = tid; t < Np * KC; t += kThreads) {
             const int j = t / KC, c = t - j * KC;
@@ -174,23 +174,26 @@ modeprod_tc_kernel(const Params P)
     } else {
         for (int j = tid; j < Np; j += kThreads) {
             const double xr = j < m ? (2.0 * P.xpts[j] - (P.ta + P.tb)) / (P.tb - P.ta) : 0.0;
-            double t0 = 1.0, t1 = xr;
+            const ff xf = ff_from_double(xr);
+            const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
+            ff t0 = {1.0f, 0.0f}, t1 = xf;
             for (int c = 0; c < KC; ++c) {
                 float v[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int k = c * E + e;
-                    double tk;
+                    float tk;
                     if (k == 0) {
-                        tk = 1.0;
+                        tk = 1.0f;
                     } else if (k == 1) {
-                        tk = xr;
+                        tk = xf.hi + xf.lo;
                     } else {
-                        tk = 2.0 * xr * t1 - t0;
+                        const ff t2 = ff_cheb_step(x2, t1, t0);
                         t0 = t1;
-                        t1 = tk;
+                        t1 = t2;
+                        tk = t2.hi + t2.lo;
                     }
-                    v[e] = (j < m && k < n) ? (float)tk : 0.0f;
+                    v[e] = (j < m && k < n) ? tk : 0.0f;
                 }
                 split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
             }
