@@ -17,8 +17,10 @@
 //    far too slow for this) and write them in the no-swizzle K-major
 //    canonical layout; B (m x n, FP64) is split once per CTA the same way;
 //  - one thread issues the split products as tcgen05.mma (M = 128, N = m
-//    rounded up to 16, K = n rounded up to the instruction K) accumulating in
-//    FP32 in TMEM, and commits to an mbarrier;
+//    rounded up to 16, K = n rounded down to the instruction K when one or two
+//    columns remain, as for the Lobatto sizes n = 2^k + 1, else rounded up)
+//    accumulating in FP32 in TMEM, and commits to an mbarrier; the remaining
+//    columns are a rank-1 (or rank-2) FP32 update in the epilogue;
 //  - the eight warps read TMEM with tcgen05.ld (warp w: lanes 32 (w % 4) ..,
 //    column chunks of 16 alternating between w < 4 and w >= 4) and store the
 //    tile transposed (coalesced along r).
@@ -37,6 +39,8 @@ using namespace tc;
 
 constexpr int kTileM = 128;
 constexpr int kThreads = 256;
+constexpr int kMaxTail = 2;   // K columns beyond the last full instruction K done in FP32
+constexpr int kMaxM = 256;
 
 template <int FORM> struct Form;
 // BF16x3: x = x0 + x1, products x1*y0 + x0*y1 + x0*y0 (small terms first).
@@ -68,11 +72,12 @@ struct Params {
     const void *X;
     const double *B;          // m x n FP64, or null: then B[j][k] = T_k(x~_j) from xpts
     const double *xpts;       // m points on [ta, tb] (used when B is null)
-    double ta, tb;
+    double xscale, xshift;    // x~ = xscale x + xshift = (2 x - ta - tb) / (tb - ta)
     float *out;
     int64_t R;
     int n, m;
-    int Kp;        // K padded to the instruction K
+    int Kp;        // K on the tensor cores: n rounded down (or up) to the instruction K
+    int tail;      // n - Kp columns (0..kMaxTail) added in FP32 in the epilogue
     int Np;        // N = m padded to 16
     int tmem_cols; // power of two >= max(32, Np)
     int *err;
@@ -120,6 +125,9 @@ __device__ __forceinline__ void split_store_chunk(const float (&v)[16 / Form<FOR
     }
 }
 
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return (float)x; }
+
 template <int FORM, typename XT>
 __global__ void __launch_bounds__(kThreads, 2)
 modeprod_tc_kernel(const Params P)
@@ -137,7 +145,8 @@ modeprod_tc_kernel(const Params P)
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;                                   // SA x [128 x Kp]
     uint8_t *sB = sA + SA * a_split_bytes;                // SB x [Np x Kp]
-    uint8_t *sX = sB + SB * b_split_bytes;                // 2 x staged X tile
+    float *sBt = reinterpret_cast<float *>(sB + SB * b_split_bytes);   // kMaxTail x Np FP32 tail columns of B
+    uint8_t *sX = reinterpret_cast<uint8_t *>(sBt + kMaxTail * kMaxM);  // 2 x staged X tile
     uint64_t *bars = reinterpret_cast<uint64_t *>(sX + 2 * stage_bytes);  // [0,1] loads, [2] mma
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
@@ -171,9 +180,13 @@ modeprod_tc_kernel(const Params P)
             }
             split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
         }
+        for (int t = tid; t < P.tail * Np; t += kThreads) {
+            const int q = t / Np, j = t - q * Np;
+            sBt[q * Np + j] = j < m ? (float)P.B[(int64_t)j * n + Kp + q] : 0.0f;
+        }
     } else {
         for (int j = tid; j < Np; j += kThreads) {
-            const double xr = j < m ? (2.0 * P.xpts[j] - (P.ta + P.tb)) / (P.tb - P.ta) : 0.0;
+            const double xr = j < m ? fma(P.xscale, P.xpts[j], P.xshift) : 0.0;
             const ff xf = ff_from_double(xr);
             const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
             ff t0 = {1.0f, 0.0f}, t1 = xf;
@@ -196,6 +209,20 @@ modeprod_tc_kernel(const Params P)
                     v[e] = (j < m && k < n) ? tk : 0.0f;
                 }
                 split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+            }
+            // the tail columns continue the same recurrence
+            for (int q = 0; q < P.tail; ++q) {
+                const int k = Kp + q;
+                float tk;
+                if (k == 1) {
+                    tk = xf.hi + xf.lo;
+                } else {
+                    const ff t2 = ff_cheb_step(x2, t1, t0);
+                    t0 = t1;
+                    t1 = t2;
+                    tk = t2.hi + t2.lo;
+                }
+                sBt[q * Np + j] = j < m ? tk : 0.0f;
             }
         }
     }
@@ -247,18 +274,33 @@ modeprod_tc_kernel(const Params P)
             // ragged last tile: plain loads straight from global memory
             xs = X + tile * kTileM * (int64_t)n;
         }
-        // split row `row` of the tile into SA parts (zero beyond the data)
+        // split row `row` of the tile into SA parts (zero beyond the data);
+        // its tail columns stay in registers for the epilogue, which this
+        // thread runs for the same row
+        float xt[kMaxTail];
         {
             const bool valid = row < rows;
             const XT *xr = xs + row * n;
-            for (int c = chalf; c < KC; c += 2) {
-                float v[E];
+#pragma unroll
+            for (int q = 0; q < kMaxTail; ++q) xt[q] = (valid && q < P.tail) ? to_f32(xr[Kp + q]) : 0.0f;
+            // two chunks per pass, loaded before anything is stored (the
+            // stores could otherwise hold the loads back)
+            for (int c0 = chalf; c0 < KC; c0 += 4) {
+                const bool two = c0 + 2 < KC;
+                float v0[E], v1[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int k = c * E + e;
-                    v[e] = (valid && k < n) ? (float)xr[k] : 0.0f;
+                    const int k = c0 * E + e;
+                    v0[e] = (valid && k < n) ? to_f32(xr[k]) : 0.0f;
                 }
-                split_store_chunk<FORM, SA>(v, sA + (uint32_t)c * (kTileM * 16) + row * 16, a_split_bytes);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = (c0 + 2) * E + e;
+                    v1[e] = (valid && two && k < n) ? to_f32(xr[k]) : 0.0f;
+                }
+                split_store_chunk<FORM, SA>(v0, sA + (uint32_t)c0 * (kTileM * 16) + row * 16, a_split_bytes);
+                if (two)
+                    split_store_chunk<FORM, SA>(v1, sA + (uint32_t)(c0 + 2) * (kTileM * 16) + row * 16, a_split_bytes);
             }
         }
         fence_async_smem();
@@ -295,13 +337,37 @@ modeprod_tc_kernel(const Params P)
             for (int c0 = ehalf * 16; c0 < Np; c0 += 32) {
                 uint32_t v[16];
                 tmem_ld16(lane_addr + c0, v);
+                // B's first tail column for these 16 columns, in registers
+                // before any store (the stores could otherwise order the loads)
+                float bt[16];
+                if (P.tail > 0) {
+                    const float4 *s4 = reinterpret_cast<const float4 *>(sBt + c0);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 f = s4[q4];
+                        bt[4 * q4] = f.x;
+                        bt[4 * q4 + 1] = f.y;
+                        bt[4 * q4 + 2] = f.z;
+                        bt[4 * q4 + 3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) bt[q] = 0.0f;
+                }
                 tmem_ld_wait();
                 if (valid) {
+                    float y[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) y[q] = fmaf(xt[0], bt[q], __uint_as_float(v[q]));
+                    if (P.tail > 1) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) y[q] = fmaf(xt[1], sBt[Np + c0 + q], y[q]);
+                    }
                     float *oc = o + (int64_t)c0 * P.R;
                     const int lim = m - c0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        if (q < lim) *oc = __uint_as_float(v[q]);
+                        if (q < lim) *oc = y[q];
                         oc += P.R;
                     }
                 }
@@ -327,7 +393,15 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
 {
     using F = Form<FORM>;
     Params P = P0;
-    P.Kp = round_up(P.n, kAlignK<FORM>);
+    // K on the tensor cores: n rounded down to the instruction K when at most
+    // kMaxTail columns remain (n = 2^k + 1, the Lobatto sizes: one column),
+    // else rounded up with zero padding
+    P.Kp = P.n / kAlignK<FORM> * kAlignK<FORM>;
+    P.tail = P.n - P.Kp;
+    if (P.Kp == 0 || P.tail > kMaxTail) {
+        P.Kp = round_up(P.n, kAlignK<FORM>);
+        P.tail = 0;
+    }
     P.Np = round_up(P.m, 16);
     int cols = 32;
     while (cols < P.Np) cols *= 2;
@@ -335,7 +409,7 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
     const size_t a_bytes = (size_t)F::SA * kTileM * P.Kp * F::EBYTES;
     const size_t b_bytes = (size_t)F::SB * P.Np * P.Kp * F::EBYTES;
     const size_t stage = (size_t)round_up(kTileM * P.n * (int)sizeof(XT), 128);
-    const size_t smem = a_bytes + b_bytes + 2 * stage + 64;
+    const size_t smem = a_bytes + b_bytes + kMaxTail * kMaxM * sizeof(float) + 2 * stage + 64;
     if (smem > 227 * 1024) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: tile does not fit in shared memory");
     auto kern = modeprod_tc_kernel<FORM, XT>;
     static bool attr_done = false;
@@ -347,8 +421,14 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
     }
     // CTAs per SM from the shared-memory budget (the occupancy query reports
     // one CTA here although two fit), capped by TMEM columns and threads.
+    static int regs = 0;
+    if (!regs) {
+        cudaFuncAttributes fa;
+        CHEB_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
+    }
     int per_sm = (int)(228 * 1024 / (smem + 1024));
-    per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
+    per_sm = std::max(1, std::min({per_sm, 2048 / kThreads, 65536 / (regs * kThreads)}));
     while (per_sm > 1 && per_sm * P.tmem_cols > 512) --per_sm;
     const int64_t ntiles = (P.R + kTileM - 1) / kTileM;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm);
@@ -377,7 +457,7 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
 {
     if (R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
-    if (m > 256) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
+    if (m > kMaxM) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
     if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
         return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
     Params P{};
@@ -385,8 +465,8 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
     P.X = X;
     P.B = B;
     P.xpts = xpts;
-    P.ta = ta;
-    P.tb = tb;
+    P.xscale = 2.0 / (tb - ta);
+    P.xshift = -(ta + tb) / (tb - ta);
     P.out = out;
     P.R = R;
     P.n = n;
@@ -410,7 +490,7 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
 {
     if (R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
-    if (m > 256) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
+    if (m > kMaxM) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
     if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
         return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
     Params P{};
@@ -418,8 +498,8 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
     P.X = X;
     P.B = B;
     P.xpts = xpts;
-    P.ta = ta;
-    P.tb = tb;
+    P.xscale = 2.0 / (tb - ta);
+    P.xshift = -(ta + tb) / (tb - ta);
     P.out = out;
     P.R = R;
     P.n = n;

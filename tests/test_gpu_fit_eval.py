@@ -172,3 +172,31 @@ def test_empty_and_invalid_arguments(ctx):
     with pytest.raises(cb.ChebError):
         cb.cheb_eval_grid(ctx, c, [dev([0.0]), dev([0.0])], a=[1.0, 0.0], b=[0.0, 1.0])
     ctx.device_status()
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_fp64_inputs_round_like_cuda(ctx, prec):
+    """The split kernels round FP64 inputs to FP32 (nearest, ties to even) before
+    splitting them. Everything they do with an FP64 coefficient starts from that
+    rounding, so evaluating FP64 coefficients must be bit-identical to evaluating
+    the same coefficients rounded first by CUDA's own conversion (torch's
+    .float() on the device): exact ties of both parities,
+    exponents across a wide range (sums stay finite), and the trailing mode
+    n = 33 (a tail column)."""
+    rng = np.random.default_rng(11)
+    shape = (5, 9, 33)
+    c = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape).astype(np.float64))
+    flat = c.reshape(-1)
+    f32 = flat[:400].astype(np.float32)
+    half_ulp = 0.5 * np.spacing(np.abs(f32)).astype(np.float64)
+    flat[:400] = f32.astype(np.float64) + np.sign(f32.astype(np.float64)) * half_ulp   # exact ties
+    flat[400:420] = np.array([1.0, -1.0, 0.0, -0.0, 1.0e20, 1.0e-30, 2.0 ** -126, 1.5, 7.0, 0.1] * 2)
+    cd = dev(c)
+    cr = cd.float().double()
+    assert not torch.equal(cd, cr)
+    xs = [dev(rng.uniform(-1, 1, k)) for k in (3, 40, 70)]
+    a = cb.cheb_eval_grid(ctx, cd, xs, prec=prec)
+    b = cb.cheb_eval_grid(ctx, cr, xs, prec=prec)
+    assert torch.equal(a, b)
+    P = dev(rng.uniform(-1, 1, (300, 3)))
+    assert torch.equal(cb.cheb_eval_points(ctx, cd, P, prec=prec), cb.cheb_eval_points(ctx, cr, P, prec=prec))
