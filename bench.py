@@ -456,8 +456,10 @@ def run_batched(args):
     ns = [n for n, _ in inst]
     form = args.form
     opts = [cb.game_opts(n, tol=1e-10, max_iter=20000, prec=form, polish_fp64=False) for n in ns]
-    for nn in sorted(set(ns)):     # warm-up: kernel attributes, workspaces
-        cb.game_solve(ctx, params[0], cb.game_opts(nn, tol=0.0, max_iter=2, prec=form, polish_fp64=False),
+    for nn in sorted(set(ns)):     # warm-up: kernel attributes, workspaces, tile tuning at this batch size
+        grp = [q for q in range(len(ns)) if ns[q] == nn]
+        cb.game_solve(ctx, [params[q] for q in grp],
+                      [cb.game_opts(nn, tol=0.0, max_iter=2, prec=form, polish_fp64=False)] * len(grp),
                       raise_on_error=False)
     torch.cuda.synchronize()
     barrier(world)
@@ -515,6 +517,7 @@ def run_batched(args):
                     "p50": float(np.percentile(errs_fp64, 50)) if errs_fp64 else None,
                     "p99": float(np.percentile(errs_fp64, 99)) if errs_fp64 else None,
                     "instances": len(errs_fp64)},
+                "tile_tuning": [ln for ln in ctx.tuning_report().splitlines() if ln],
                 "clocks": clocks}
         print(json.dumps(line))
     ctx.close()

@@ -103,6 +103,25 @@ CHEB_API int cheb_profile_count(cheb_ctx *ctx);
 CHEB_API cheb_status cheb_profile_get(cheb_ctx *ctx, int idx, char *name, int name_len,
                                       int64_t *launches, double *total_ms);
 
+/* Tile-shape tuning of the split-precision game update. The paper has no
+ * counterpart beyond its block-size sweep of the parallel evaluation (Section
+ * 4, prior art for this): the library picks, per precision form, node count n
+ * and batch-size class (1, then factors of 4), the MMA column chunk of the
+ * player update (hence its N, shared memory and TMEM) and the CTAs per SM, by
+ * timing every configuration on the caller's own first iteration of
+ * game_solve before that solve's iterations are captured into a CUDA graph.
+ * The timed runs are that iteration's own work and leave every result
+ * unchanged; all configurations compute bit-identical iterates.
+ * cheb_set_tuning: mode 0 tunes on first use (the default), 1 always uses the
+ * default shape, 2 + k forces configuration k (k = 4 * chunk index + CTAs per
+ * SM; game_solve returns CHEB_EINVAL if it does not exist for an n). Any
+ * other mode is CHEB_EINVAL. Choices made so far are kept across modes.
+ * cheb_tuning_report writes one line per tuned shape (its key, the chosen
+ * configuration and the time of every configuration tried) into buf,
+ * NUL-terminated and cut at buf_len bytes. Neither call launches work. */
+CHEB_API cheb_status cheb_set_tuning(cheb_ctx *ctx, int mode);
+CHEB_API cheb_status cheb_tuning_report(cheb_ctx *ctx, char *buf, int64_t buf_len);
+
 /*
  * cheb_fit - coefficients of the d-dimensional Chebyshev interpolant.
  *

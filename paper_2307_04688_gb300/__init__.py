@@ -71,6 +71,17 @@ class Context:
         """Turn per-kernel CUDA-event timing on or off (clears the totals)."""
         check(load().cheb_profile(self._h, int(bool(enable))))
 
+    def set_tuning(self, mode: int) -> None:
+        """Tile-shape tuning of the split game update: 0 tune on first use (default),
+        1 default shapes, 2 + k force configuration k (4 * chunk index + CTAs per SM)."""
+        check(load().cheb_set_tuning(self._h, int(mode)))
+
+    def tuning_report(self) -> str:
+        """One line per tuned shape: key, chosen configuration, time of each one tried."""
+        buf = C.create_string_buffer(1 << 16)
+        check(load().cheb_tuning_report(self._h, buf, len(buf)))
+        return buf.value.decode()
+
     def profile_read(self) -> dict:
         """{kernel name: (launches, total milliseconds)} since profiling was turned on."""
         L = load()

@@ -294,6 +294,28 @@ cheb_status cheb_profile_get(cheb_ctx *ctx, int idx, char *name, int name_len, i
     return CHEB_OK;
 }
 
+cheb_status cheb_set_tuning(cheb_ctx *ctx, int mode)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    if (mode < 0 || mode > 2 + 4 * 3) return fail(CHEB_EINVAL, "cheb_set_tuning: mode must be 0, 1 or 2 + a configuration");
+    ctx->tune_mode = mode;
+    return CHEB_OK;
+}
+
+cheb_status cheb_tuning_report(cheb_ctx *ctx, char *buf, int64_t buf_len)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!buf || buf_len < 1) return fail(CHEB_EINVAL, "cheb_tuning_report: need a buffer");
+    std::string out;
+    for (const auto &kv : ctx->game_tune) out += "game_player_tc " + kv.first + ": " + kv.second.second + "\n";
+    const size_t nb = std::min<size_t>(out.size(), (size_t)buf_len - 1);
+    std::memcpy(buf, out.data(), nb);
+    buf[nb] = 0;
+    return CHEB_OK;
+}
+
 cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *values, double *coeffs,
                      void *stream)
 {

@@ -55,6 +55,10 @@ struct cheb_ctx {
     std::map<int, double *> dct;        // n -> device n x n DCT-I matrix (FP64)
     cheb::DevBuf game;                  // game state of one game_solve call
     cheb::DevBuf game_aux;
+    // tile-shape tuning (cheb_set_tuning): 0 tune on first use, 1 default
+    // shapes, 2 + k force configuration k; tuned choices by shape key
+    int tune_mode = 0;
+    std::map<std::string, std::pair<int, std::string>> game_tune;
     int *d_error = nullptr;             // device error word written by bounded waits
     // kernel timing (cheb_profile): events around every library launch
     bool prof_on = false;

@@ -397,6 +397,13 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         return CHEB_OK;
     };
 
+    // ---- tile shapes of the split player update, timed on this group ----
+    if (prec != CHEB_FP64) {
+        next_state_kernel<<<dim3(node_blocks, B), 128, 0, st>>>(d_inst, d_stat);
+        CHEB_CUDA_TRY(cudaGetLastError());
+        if ((r = game_tc_tune(ctx, d_inst, d_stat, B, J, n, prec, st))) return r;
+    }
+
     // ---- chunks of iterations, captured once into a CUDA graph ----
     const int chunk = (int)std::min<int64_t>(max_iter, 32);
     const bool use_graph = !ctx->prof_on;

@@ -148,6 +148,13 @@ size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec);
 void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws);
 cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, const GameDev *hinst, int B,
                            int J, int n, int NP, int prec, uint8_t *ws, cudaStream_t st);
+// Tile-shape tuner: before the first iteration of a group (X of that iteration
+// already computed), time every tile configuration of the split player update
+// on the group itself and keep the fastest for (form, n, batch class) in the
+// context. The runs are the first iteration's own work (deterministic; the
+// real iteration rewrites the same values), so they change no result.
+cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int J, int n, int prec,
+                         cudaStream_t st);
 
 }  // namespace game
 }  // namespace cheb

@@ -20,7 +20,9 @@
 //    (Newton in FP32 from the previous control, the value at the maximiser in
 //    FP64) and writes the new control, value and the FP64 residual.
 #include <algorithm>
+#include <cstdio>
 #include <string>
+#include <vector>
 
 #include "game_internal.cuh"
 #include "tc_common.cuh"
@@ -51,13 +53,17 @@ template <> struct GForm<CHEB_TF32X3> {
     __device__ static constexpr int pb(int p) { return p == 1 ? 1 : 0; }
 };
 
-template <int FORM, int NN> struct Shape {
+// The column chunk (k_i values per chunk, CH) is the tuned tile shape: it sets
+// the MMA N (CH x NBP <= 256), the shared memory of the two B stages and the
+// TMEM columns, hence how many CTAs fit on an SM.
+template <int FORM, int NN, int CH> struct Shape {
     using F = GForm<FORM>;
     static constexpr int NBP = (NN + 15) / 16 * 16;                 // k_b padded
     static constexpr int KP = (NN + F::KALIGN - 1) / F::KALIGN * F::KALIGN;   // k_a padded
     static constexpr int E = 16 / F::EB;                            // K elements per 16 bytes
     static constexpr int KC = KP / E;                               // 16-byte chunks along K
-    static constexpr int CHKI = 256 / NBP < NN ? 256 / NBP : NN;    // k_i per column chunk
+    static constexpr int CHKI = CH;                                 // k_i per column chunk
+    static_assert(CH >= 1 && CH <= NN && CH * NBP <= 256, "column chunk out of range");
     static constexpr int NCH = (NN + CHKI - 1) / CHKI;              // column chunks
     static constexpr int NC = CHKI * NBP;                           // columns of a stored chunk
     static constexpr int SPLIT_BYTES = NC * KP * F::EB;             // one split part of a chunk
@@ -68,6 +74,14 @@ template <int FORM, int NN> struct Shape {
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) + 128;
 };
+
+// Column chunks the tuner tries for each node count; the first is the default
+// (the widest chunk: fewest MMA rounds, one CTA per SM).
+template <int NN> struct Chunks;
+template <> struct Chunks<5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };
+template <> struct Chunks<9> { static constexpr int count = 2, v0 = 9, v1 = 3, v2 = 3; };
+template <> struct Chunks<17> { static constexpr int count = 3, v0 = 8, v1 = 4, v2 = 2; };
+template <> struct Chunks<33> { static constexpr int count = 3, v0 = 5, v1 = 2, v2 = 1; };
 
 // ---- helpers -------------------------------------------------------------------
 // T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
@@ -135,10 +149,10 @@ __device__ __forceinline__ void other_modes(int i, int &a, int &b)
 
 // ---- B operand: split C_i once per iteration -----------------------------------
 // Thread per (instance, player, chunk, row of the chunk, 16-byte K chunk).
-template <int FORM, int NN>
+template <int FORM, int NN, int CH>
 __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats, int B)
 {
-    using S = Shape<FORM, NN>;
+    using S = Shape<FORM, NN, CH>;
     using F = GForm<FORM>;
     const int per_item = S::NC * S::KC;
     const int64_t total = (int64_t)B * 3 * S::NCH * per_item;
@@ -198,11 +212,11 @@ __device__ __forceinline__ void objective_f32(const float (&w)[NN], float xc, fl
     W2 = -h + delta * slope * slope * s2;
 }
 
-template <int FORM, int NN>
+template <int FORM, int NN, int CH>
 __global__ void __launch_bounds__(kThreads, 1)
 game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B, int *err)
 {
-    using S = Shape<FORM, NN>;
+    using S = Shape<FORM, NN, CH>;
     using F = GForm<FORM>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;                                         // SA x [128 x KP]
@@ -439,59 +453,153 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     if (warp == 0) tmem_dealloc(tmem, S::TMEM_ALLOC);
 }
 
-template <int FORM, int NN>
-cheb_status launch_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, cudaStream_t st)
+// Most CTAs of one variant that fit on an SM (shared memory, registers, TMEM).
+template <int FORM, int NN, int CH>
+cheb_status max_ctas(int *out)
 {
-    using S = Shape<FORM, NN>;
-    static_assert(S::SMEM <= 227 * 1024, "game player tile does not fit in shared memory");
-    {
-        const int64_t total = (int64_t)B * 3 * S::NCH * S::NC * S::KC;
-        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-        ProfScope prof("game_bprep n=" + std::to_string(NN), st);
-        game_bprep_kernel<FORM, NN><<<blocks, 256, 0, st>>>(d_inst, d_stat, B);
-        CHEB_CUDA_TRY(cudaGetLastError());
-    }
-    auto kern = game_player_tc_kernel<FORM, NN>;
-    static bool attr = false;
-    if (!attr) {
+    using S = Shape<FORM, NN, CH>;
+    auto kern = game_player_tc_kernel<FORM, NN, CH>;
+    static int cached = 0;
+    if (!cached) {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
-        attr = true;
+        cudaFuncAttributes fa;
+        CHEB_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        const int regs = std::max(8, (fa.numRegs + 7) / 8 * 8);
+        int k = (int)(228 * 1024 / (S::SMEM + 1024));
+        k = std::min({k, 65536 / (regs * kThreads), 512 / S::TMEM_ALLOC, 2048 / kThreads, 3});
+        cached = std::max(1, k);
+    }
+    *out = cached;
+    return CHEB_OK;
+}
+
+template <int FORM, int NN, int CH>
+cheb_status launch_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int per_sm, cudaStream_t st)
+{
+    using S = Shape<FORM, NN, CH>;
+    static_assert(S::SMEM <= 227 * 1024, "game player tile does not fit in shared memory");
+    int kmax = 1;
+    cheb_status r = max_ctas<FORM, NN, CH>(&kmax);
+    if (r) return r;
+    per_sm = std::max(1, std::min(per_sm, kmax));
+    {
+        const int64_t total = (int64_t)B * 3 * S::NCH * S::NC * S::KC;
+        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+        ProfScope prof("game_bprep n=" + std::to_string(NN) + " chunk=" + std::to_string(CH), st);
+        game_bprep_kernel<FORM, NN, CH><<<blocks, 256, 0, st>>>(d_inst, d_stat, B);
+        CHEB_CUDA_TRY(cudaGetLastError());
     }
     const int tiles = (NN * NN * NN + kTile - 1) / kTile;
     const int64_t items = (int64_t)B * 3 * tiles;
-    const int grid = (int)std::min<int64_t>(items, ctx->num_sms);
-    ProfScope prof("game_player_tc n=" + std::to_string(NN), st);
-    kern<<<grid, kThreads, S::SMEM, st>>>(d_inst, d_stat, B, ctx->d_error);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)ctx->num_sms * per_sm);
+    ProfScope prof("game_player_tc n=" + std::to_string(NN) + " chunk=" + std::to_string(CH) +
+                       " ctas/SM=" + std::to_string(per_sm),
+                   st);
+    game_player_tc_kernel<FORM, NN, CH><<<grid, kThreads, S::SMEM, st>>>(d_inst, d_stat, B, ctx->d_error);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
 
+// A tile configuration: chunk variant c (index into Chunks<NN>) and CTAs per SM k.
+constexpr int cfg_of(int c, int k) { return c * 4 + k; }
+
+template <int FORM, int NN>
+cheb_status run_cfg(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int cfg, cudaStream_t st)
+{
+    using C = Chunks<NN>;
+    const int c = cfg / 4, k = cfg % 4;
+    if (c == 1 && C::count > 1) return launch_player<FORM, NN, C::v1>(ctx, d_inst, d_stat, B, k, st);
+    if (c == 2 && C::count > 2) return launch_player<FORM, NN, C::v2>(ctx, d_inst, d_stat, B, k, st);
+    return launch_player<FORM, NN, C::v0>(ctx, d_inst, d_stat, B, k, st);
+}
+
+// The configurations the tuner tries for NN: every chunk variant at every CTA
+// count from 1 to what fits.
+template <int FORM, int NN>
+cheb_status candidates(std::vector<int> *out)
+{
+    using C = Chunks<NN>;
+    int k[3] = {1, 1, 1};
+    cheb_status r = max_ctas<FORM, NN, C::v0>(&k[0]);
+    if (!r && C::count > 1) r = max_ctas<FORM, NN, C::v1>(&k[1]);
+    if (!r && C::count > 2) r = max_ctas<FORM, NN, C::v2>(&k[2]);
+    if (r) return r;
+    out->clear();
+    for (int c = 0; c < C::count; ++c)
+        for (int kk = 1; kk <= k[c]; ++kk) out->push_back(cfg_of(c, kk));
+    return CHEB_OK;
+}
+
+template <int FORM, int NN>
+std::string describe(int cfg)
+{
+    using C = Chunks<NN>;
+    const int c = cfg / 4, chunk = c == 0 ? C::v0 : c == 1 ? C::v1 : C::v2;
+    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(chunk * ((NN + 15) / 16 * 16)) +
+           ") ctas/SM=" + std::to_string(cfg % 4);
+}
+
 template <int FORM>
-cheb_status dispatch_n(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, cudaStream_t st)
+cheb_status dispatch_n(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, int cfg, cudaStream_t st)
 {
     switch (n) {
-    case 5: return launch_player<FORM, 5>(ctx, d_inst, d_stat, B, st);
-    case 9: return launch_player<FORM, 9>(ctx, d_inst, d_stat, B, st);
-    case 17: return launch_player<FORM, 17>(ctx, d_inst, d_stat, B, st);
-    case 33: return launch_player<FORM, 33>(ctx, d_inst, d_stat, B, st);
+    case 5: return run_cfg<FORM, 5>(ctx, d_inst, d_stat, B, cfg, st);
+    case 9: return run_cfg<FORM, 9>(ctx, d_inst, d_stat, B, cfg, st);
+    case 17: return run_cfg<FORM, 17>(ctx, d_inst, d_stat, B, cfg, st);
+    case 33: return run_cfg<FORM, 33>(ctx, d_inst, d_stat, B, cfg, st);
     default: return fail(CHEB_EUNSUPPORTED, "game_solve: split precision supports n in {5, 9, 17, 33}");
     }
 }
 
-template <int FORM, int NN> constexpr size_t chunk_bytes() { return Shape<FORM, NN>::CHUNK_BYTES; }
-template <int FORM, int NN> constexpr int nchunks() { return Shape<FORM, NN>::NCH; }
+template <int FORM>
+cheb_status candidates_n(int n, std::vector<int> *out)
+{
+    switch (n) {
+    case 5: return candidates<FORM, 5>(out);
+    case 9: return candidates<FORM, 9>(out);
+    case 17: return candidates<FORM, 17>(out);
+    case 33: return candidates<FORM, 33>(out);
+    default: return fail(CHEB_EUNSUPPORTED, "game_solve: split precision supports n in {5, 9, 17, 33}");
+    }
+}
 
+template <int FORM>
+std::string describe_n(int n, int cfg)
+{
+    switch (n) {
+    case 5: return describe<FORM, 5>(cfg);
+    case 9: return describe<FORM, 9>(cfg);
+    case 17: return describe<FORM, 17>(cfg);
+    default: return describe<FORM, 33>(cfg);
+    }
+}
+
+template <int FORM, int NN, int CH> constexpr size_t variant_bytes()
+{
+    return Shape<FORM, NN, CH>::CHUNK_BYTES * Shape<FORM, NN, CH>::NCH;
+}
+
+template <int FORM, int NN> constexpr size_t max_bytes()
+{
+    using C = Chunks<NN>;
+    size_t b = variant_bytes<FORM, NN, C::v0>();
+    b = std::max(b, variant_bytes<FORM, NN, C::v1>());
+    return std::max(b, variant_bytes<FORM, NN, C::v2>());
+}
+
+// B-operand bytes per player, the largest over the chunk variants (the
+// workspace serves whichever variant runs)
 size_t bsplit_bytes(int n, int prec)
 {
-#define CHEB_BS(FORM)                                                                   \
-    switch (n) {                                                                      \
-    case 5: return chunk_bytes<FORM, 5>() * nchunks<FORM, 5>();                       \
-    case 9: return chunk_bytes<FORM, 9>() * nchunks<FORM, 9>();                       \
-    case 17: return chunk_bytes<FORM, 17>() * nchunks<FORM, 17>();                    \
-    case 33: return chunk_bytes<FORM, 33>() * nchunks<FORM, 33>();                    \
-    default: return 0;                                                                \
+#define CHEB_BS(FORM)                                   \
+    switch (n) {                                      \
+    case 5: return max_bytes<FORM, 5>();              \
+    case 9: return max_bytes<FORM, 9>();              \
+    case 17: return max_bytes<FORM, 17>();            \
+    case 33: return max_bytes<FORM, 33>();            \
+    default: return 0;                                \
     }
     switch (prec) {
     case CHEB_BF16X3: CHEB_BS(CHEB_BF16X3)
@@ -500,6 +608,57 @@ size_t bsplit_bytes(int n, int prec)
     default: return 0;
     }
 #undef CHEB_BS
+}
+
+cheb_status run_any(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, int prec, int cfg,
+                    cudaStream_t st)
+{
+    switch (prec) {
+    case CHEB_BF16X3: return dispatch_n<CHEB_BF16X3>(ctx, d_inst, d_stat, B, n, cfg, st);
+    case CHEB_BF16X6: return dispatch_n<CHEB_BF16X6>(ctx, d_inst, d_stat, B, n, cfg, st);
+    case CHEB_TF32X3: return dispatch_n<CHEB_TF32X3>(ctx, d_inst, d_stat, B, n, cfg, st);
+    default: return fail(CHEB_EINVAL, "game_solve: bad precision");
+    }
+}
+
+cheb_status candidates_any(int n, int prec, std::vector<int> *out)
+{
+    switch (prec) {
+    case CHEB_BF16X3: return candidates_n<CHEB_BF16X3>(n, out);
+    case CHEB_BF16X6: return candidates_n<CHEB_BF16X6>(n, out);
+    case CHEB_TF32X3: return candidates_n<CHEB_TF32X3>(n, out);
+    default: return fail(CHEB_EINVAL, "game_solve: bad precision");
+    }
+}
+
+std::string describe_any(int n, int prec, int cfg)
+{
+    switch (prec) {
+    case CHEB_BF16X3: return describe_n<CHEB_BF16X3>(n, cfg);
+    case CHEB_BF16X6: return describe_n<CHEB_BF16X6>(n, cfg);
+    default: return describe_n<CHEB_TF32X3>(n, cfg);
+    }
+}
+
+const char *form_name(int prec)
+{
+    return prec == CHEB_BF16X3 ? "bf16x3" : prec == CHEB_BF16X6 ? "bf16x6" : "tf32x3";
+}
+
+// batch-size class of a tuning entry: 0 for B = 1, then one class per factor 4
+int batch_class(int B)
+{
+    int c = 0;
+    while (B > 1 && c < 8) {
+        B = (B + 3) / 4;
+        ++c;
+    }
+    return c;
+}
+
+std::string tune_key(int prec, int n, int B)
+{
+    return std::string(form_name(prec)) + " n=" + std::to_string(n) + " batch class " + std::to_string(batch_class(B));
 }
 
 }  // namespace
@@ -526,12 +685,68 @@ cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_sta
     (void)NP;
     (void)ws;
     if (J != 3) return fail(CHEB_EUNSUPPORTED, "game_solve: split precision needs J = 3");
-    switch (prec) {
-    case CHEB_BF16X3: return dispatch_n<CHEB_BF16X3>(ctx, d_inst, d_stat, B, n, st);
-    case CHEB_BF16X6: return dispatch_n<CHEB_BF16X6>(ctx, d_inst, d_stat, B, n, st);
-    case CHEB_TF32X3: return dispatch_n<CHEB_TF32X3>(ctx, d_inst, d_stat, B, n, st);
-    default: return fail(CHEB_EINVAL, "game_solve: bad precision");
+    int cfg = cfg_of(0, 1);   // the default shape
+    if (ctx->tune_mode >= 2) {
+        std::vector<int> cands;
+        cheb_status r = candidates_any(n, prec, &cands);
+        if (r) return r;
+        cfg = ctx->tune_mode - 2;
+        if (std::find(cands.begin(), cands.end(), cfg) == cands.end())
+            return fail(CHEB_EINVAL, "game_solve: the forced tile configuration does not exist for n = " +
+                                         std::to_string(n));
+    } else if (ctx->tune_mode == 0) {
+        auto it = ctx->game_tune.find(tune_key(prec, n, B));
+        if (it != ctx->game_tune.end()) cfg = it->second.first;
     }
+    return run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st);
+}
+
+cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int J, int n, int prec,
+                         cudaStream_t st)
+{
+    if (prec == CHEB_FP64 || J != 3 || ctx->tune_mode != 0) return CHEB_OK;
+    const std::string key = tune_key(prec, n, B);
+    if (ctx->game_tune.count(key)) return CHEB_OK;
+    std::vector<int> cands;
+    cheb_status r = candidates_any(n, prec, &cands);
+    if (r) return r;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CHEB_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return CHEB_OK;   // cannot time inside a capture: default shape
+    cudaEvent_t e0, e1;
+    CHEB_CUDA_TRY(cudaEventCreate(&e0));
+    CHEB_CUDA_TRY(cudaEventCreate(&e1));
+    int best = cands[0];
+    float best_ms = 0.0f;
+    std::string times;
+    for (size_t c = 0; c < cands.size() && r == CHEB_OK; ++c) {
+        const int cfg = cands[c];
+        if ((r = run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3 && r == CHEB_OK; ++rep) r = run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st);
+        cudaEventRecord(e1, st);
+        if (r) break;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+            r = cuda_fail(ce, "game tile tuning");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.0f;
+        char buf[64];
+        std::snprintf(buf, sizeof(buf), " %.1f us", 1000.0f * ms);
+        times += (c ? ", " : "") + describe_any(n, prec, cfg) + buf;
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r;
+    ctx->game_tune[key] = {best, describe_any(n, prec, best) + " [tried: " + times + "]"};
+    return CHEB_OK;
 }
 
 }  // namespace game
