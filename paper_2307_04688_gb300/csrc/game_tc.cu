@@ -13,6 +13,10 @@
 //    16) is split once per iteration by game_bprep_kernel into the canonical
 //    shared-memory layout, chunk by chunk (<= 256 columns), and each chunk is
 //    brought in by one bulk copy (TMA engine), double-buffered;
+//  - for n = 16 q + 1 (17, 33) the tensor cores take k_a, k_b < n - 1 with no
+//    padding, and the k_a = n - 1 row and k_b = n - 1 column of C_i become two
+//    FP32 dot products per (node, k_i) in the epilogue, overlapping the next
+//    chunk's MMA (a third of the MMA work at n = 33, half at n = 17);
 //  - tcgen05.mma accumulates the split products of a chunk in TMEM (FP32);
 //  - the epilogue reads TMEM, multiplies by T_{k_b}(x_b(j)) (kept in
 //    registers) and writes w_j[k_i] to shared memory;
@@ -58,8 +62,13 @@ template <> struct GForm<CHEB_TF32X3> {
 // TMEM columns, hence how many CTAs fit on an SM.
 template <int FORM, int NN, int CH> struct Shape {
     using F = GForm<FORM>;
-    static constexpr int NBP = (NN + 15) / 16 * 16;                 // k_b padded
-    static constexpr int KP = (NN + F::KALIGN - 1) / F::KALIGN * F::KALIGN;   // k_a padded
+    // n = 16 q + 1 (the Lobatto sizes 17, 33): the tensor cores take k_a, k_b
+    // < n - 1 with no padding; the k_a = n - 1 row and the k_b = n - 1 column
+    // of C_i are two FP32 dot products per (node, k_i) in the epilogue
+    static constexpr int TAIL = (NN > 16 && (NN - 1) % 16 == 0) ? 1 : 0;
+    static constexpr int NM = NN - TAIL;                              // k_a, k_b on the tensor cores
+    static constexpr int NBP = (NM + 15) / 16 * 16;                 // k_b padded
+    static constexpr int KP = (NM + F::KALIGN - 1) / F::KALIGN * F::KALIGN;   // k_a padded
     static constexpr int E = 16 / F::EB;                            // K elements per 16 bytes
     static constexpr int KC = KP / E;                               // 16-byte chunks along K
     static constexpr int CHKI = CH;                                 // k_i per column chunk
@@ -71,8 +80,15 @@ template <int FORM, int NN, int CH> struct Shape {
     static constexpr int A_SPLIT = kTile * KP * F::EB;
     static constexpr int TMEM_COLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;   // one buffer
     static constexpr int TMEM_ALLOC = 2 * TMEM_COLS;                // two accumulators (<= 512)
+    // FP32 tail coefficients per player: Ca[k_i][k_b] = C[k_i, n-1, k_b] (k_b < n),
+    // Cb[k_i][k_a] = C[k_i, k_a, n-1] (k_a < n - 1)
+    static constexpr int TAIL_FLOATS = TAIL ? 2 * NN * NN : 0;
+    static constexpr size_t PLAYER_BYTES =     // a multiple of 128: every chunk starts 16-byte aligned
+        ((size_t)NCH * CHUNK_BYTES + (size_t)TAIL_FLOATS * sizeof(float) + 127) / 128 * 128;
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
-                                   (size_t)NN * kTile * sizeof(float) + 128;
+                                   (size_t)NN * kTile * sizeof(float) +              // w
+                                   (size_t)TAIL * NN * kTile * sizeof(float) +       // T_{k_a} per row
+                                   (size_t)TAIL_FLOATS * sizeof(float) + 128;
 };
 
 // Column chunks the tuner tries for each node count; the first is the default
@@ -80,8 +96,8 @@ template <int FORM, int NN, int CH> struct Shape {
 template <int NN> struct Chunks;
 template <> struct Chunks<5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };
 template <> struct Chunks<9> { static constexpr int count = 2, v0 = 9, v1 = 3, v2 = 3; };
-template <> struct Chunks<17> { static constexpr int count = 3, v0 = 8, v1 = 4, v2 = 2; };
-template <> struct Chunks<33> { static constexpr int count = 3, v0 = 5, v1 = 2, v2 = 1; };
+template <> struct Chunks<17> { static constexpr int count = 3, v0 = 9, v1 = 6, v2 = 3; };    // N = 144, 96, 48
+template <> struct Chunks<33> { static constexpr int count = 3, v0 = 7, v1 = 5, v2 = 3; };    // N = 224, 160, 96
 
 // ---- helpers -------------------------------------------------------------------
 // T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
@@ -177,13 +193,40 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
 #pragma unroll
         for (int k = 0; k < S::E; ++k) {
             const int ka = kc * S::E + k;
-            v[k] = (ki < NN && kb < NN && ka < NN)
+            v[k] = (ki < NN && kb < S::NM && ka < S::NM)
                        ? (float)C[ki * si + ka * sa + kb * sb]
                        : 0.0f;
         }
-        uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + ((size_t)i * S::NCH + c) * S::CHUNK_BYTES +
+        uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES + (size_t)c * S::CHUNK_BYTES +
                        (size_t)kc * (S::NC * 16) + (size_t)row * 16;
         split_store16<FORM, F::SB>(v, dst, S::SPLIT_BYTES);
+    }
+    if constexpr (S::TAIL) {
+        // the FP32 tail coefficients, after each player's chunks
+        const int64_t ttot = (int64_t)B * 3 * S::TAIL_FLOATS;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ttot;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int e = (int)(t % S::TAIL_FLOATS);
+            const int i = (int)((t / S::TAIL_FLOATS) % 3);
+            const int q = (int)(t / (S::TAIL_FLOATS * 3));
+            if (stats[q].done || stats[q].mode != 1) continue;
+            const GameDev &g = insts[q];
+            int a, b;
+            other_modes(i, a, b);
+            const int si = i == 0 ? NN * NN : i == 1 ? NN : 1;
+            const int sa = a == 0 ? NN * NN : a == 1 ? NN : 1;
+            const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
+            const double *C = g.C + (size_t)i * g.NP;
+            const int half = e / (NN * NN), r = e - half * NN * NN, ki = r / NN, k = r - ki * NN;
+            float v;
+            if (half == 0)
+                v = (float)C[ki * si + (NN - 1) * sa + k * sb];                          // Ca[ki][kb = k]
+            else
+                v = k < NN - 1 ? (float)C[ki * si + k * sa + (NN - 1) * sb] : 0.0f;    // Cb[ki][ka = k]
+            float *dst = reinterpret_cast<float *>(static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES +
+                                                   (size_t)S::NCH * S::CHUNK_BYTES);
+            dst[e] = v;
+        }
     }
 }
 
@@ -222,7 +265,9 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     uint8_t *sA = smem;                                         // SA x [128 x KP]
     uint8_t *sB = sA + F::SA * S::A_SPLIT;                      // 2 stages x CHUNK_BYTES
     float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(w_s + NN * kTile);   // [0,1] B loads, [2,3] mma per accumulator
+    float *ta_s = w_s + NN * kTile;                                   // [NN][128] T_{k_a} of each row (TAIL)
+    float *ct_s = ta_s + S::TAIL * NN * kTile;                        // tail coefficients Ca, Cb (TAIL)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ct_s + S::TAIL_FLOATS);   // [0,1] B loads, [2,3] mma per accumulator
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -263,7 +308,11 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const GameDev &g = insts[q];
         int a, b;
         other_modes(i, a, b);
-        const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::NCH * S::CHUNK_BYTES;
+        const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
+        if constexpr (S::TAIL) {
+            const float *tsrc = reinterpret_cast<const float *>(bsrc + (size_t)S::NCH * S::CHUNK_BYTES);
+            for (int e = tid; e < S::TAIL_FLOATS; e += kThreads) ct_s[e] = tsrc[e];
+        }
         if (tid == 0) {
             for (int c = 0; c < 2 && c < S::NCH; ++c) {
                 mbar_arrive_expect_tx(&bars[c], S::CHUNK_BYTES);
@@ -275,6 +324,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const int j = t * kTile + row;
         const bool valid = j < NP;
         float Tb[S::NBP];
+        float tb_last = 0.0f;    // T_{n-1}(x_b) (TAIL)
         {
             float Ta[NN], Tbn[NN];
             const double xa = valid ? g.X[a * NP + j] : 0.0;
@@ -282,7 +332,14 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             cheb_row_f32<NN>(xa, Ta);
             cheb_row_f32<NN>(xb, Tbn);
 #pragma unroll
-            for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < NN) ? Tbn[k] : 0.0f;
+            for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < S::NM) ? Tbn[k] : 0.0f;
+            if constexpr (S::TAIL) {
+                tb_last = valid ? Tbn[NN - 1] : 0.0f;
+                if (half == 0) {
+#pragma unroll
+                    for (int k = 0; k < NN; ++k) ta_s[k * kTile + row] = valid ? Ta[k] : 0.0f;
+                }
+            }
 #pragma unroll
             for (int kc = 0; kc < S::KC; ++kc) {
                 if ((kc & 1) != half) continue;
@@ -290,7 +347,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 #pragma unroll
                 for (int e = 0; e < S::E; ++e) {
                     const int k = kc * S::E + e;
-                    v[e] = (valid && k < NN) ? Ta[k < NN ? k : 0] : 0.0f;
+                    v[e] = (valid && k < S::NM) ? Ta[k < S::NM ? k : 0] : 0.0f;
                 }
                 split_store16<FORM, F::SA>(v, sA + (uint32_t)kc * (kTile * 16) + row * 16, S::A_SPLIT);
             }
@@ -358,6 +415,20 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                     for (int g16 = 0; g16 < S::NBP / 16; ++g16)
 #pragma unroll
                         for (int e = 0; e < 16; ++e) acc = fmaf(__uint_as_float(v[g16][e]), Tb[g16 * 16 + e], acc);
+                    if constexpr (S::TAIL) {
+                        // T_{n-1}(x_a) sum_{k_b} C[k_i, n-1, k_b] T_{k_b}(x_b)
+                        //   + T_{n-1}(x_b) sum_{k_a < n-1} C[k_i, k_a, n-1] T_{k_a}(x_a)
+                        const int ki = c * S::CHKI + kl;
+                        const float *ca = ct_s + ki * NN;
+                        const float *cb = ct_s + NN * NN + ki * NN;
+                        float ta_dot = ca[NN - 1] * tb_last, tb_dot = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < S::NM; ++k) {
+                            ta_dot = fmaf(ca[k], Tb[k], ta_dot);
+                            tb_dot = fmaf(cb[k], ta_s[k * kTile + r], tb_dot);
+                        }
+                        acc = fmaf(ta_s[(NN - 1) * kTile + r], ta_dot, fmaf(tb_last, tb_dot, acc));
+                    }
                     w_s[(c * S::CHKI + kl) * kTile + r] = acc;
                 }
             }
@@ -537,7 +608,8 @@ std::string describe(int cfg)
 {
     using C = Chunks<NN>;
     const int c = cfg / 4, chunk = c == 0 ? C::v0 : c == 1 ? C::v1 : C::v2;
-    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(chunk * ((NN + 15) / 16 * 16)) +
+    constexpr int nbp = Shape<FORM, NN, C::v0>::NBP;
+    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(chunk * nbp) +
            ") ctas/SM=" + std::to_string(cfg % 4);
 }
 
@@ -578,7 +650,7 @@ std::string describe_n(int n, int cfg)
 
 template <int FORM, int NN, int CH> constexpr size_t variant_bytes()
 {
-    return Shape<FORM, NN, CH>::CHUNK_BYTES * Shape<FORM, NN, CH>::NCH;
+    return Shape<FORM, NN, CH>::PLAYER_BYTES;
 }
 
 template <int FORM, int NN> constexpr size_t max_bytes()
