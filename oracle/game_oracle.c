@@ -41,6 +41,7 @@ void orc_deriv_coeffs(int n, const double *p, double *q);
 double orc_series(int n, const double *p, double x);
 void orc_fit_nd(int d, const int *n, const double *Gamma, double *coef);
 double orc_eval_nested(int d, const int *n, const double *coef, const double *xref, double *work);
+double orc_eval_direct(int d, const int *n, const double *coef, const double *xref);
 
 typedef struct {
     int J;
@@ -371,4 +372,45 @@ void orc_game_lq(const orc_game_params *P, double h, int R, double *Qo, double *
             fo[(size_t)r * J + i] = f[i];
         }
     }
+}
+
+/* Equilibrium time paths (Section 4: the emission and pollution-stock paths
+ * along the equilibrium strategy). The feedback policy of player i is the
+ * Chebyshev interpolant of its nodal controls on [0, P_M]^J (Definition 3.2,
+ * fitted by eq. (forcoef)), clamped to [0, U_M]; from each initial stock, T
+ * explicit steps of the dynamics with the discretisation's time step h:
+ *     p_{t+1} = p_t + h g(p_t, u(p_t)).
+ * u_nodal: J x n^J nodal controls (row-major, last player fastest); p0: K x J;
+ * p_path: K x (T + 1) x J (p_path[k][0] = p0[k]); u_path: K x T x J or NULL. */
+void orc_game_paths(const orc_game_params *P, const orc_game_opts *O, const double *u_nodal, long K,
+                    const double *p0, long T, double *p_path, double *u_path)
+{
+    const int J = P->J;
+    const long NP = ipow(O->n, J);
+    int nd[4];
+    for (int s = 0; s < J; ++s) nd[s] = O->n;
+    double *coef = (double *)malloc(sizeof(double) * (size_t)J * (size_t)NP);
+    for (int i = 0; i < J; ++i) orc_fit_nd(J, nd, u_nodal + (size_t)i * NP, coef + (size_t)i * NP);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < K; ++k) {
+        double p[4], u[4], g[4], xref[4];
+        for (int s = 0; s < J; ++s) {
+            p[s] = p0[(size_t)k * J + s];
+            p_path[((size_t)k * (T + 1)) * J + s] = p[s];
+        }
+        for (long t = 0; t < T; ++t) {
+            for (int s = 0; s < J; ++s) xref[s] = 2.0 * p[s] / O->P_M - 1.0;
+            for (int i = 0; i < J; ++i) {
+                const double v = orc_eval_direct(J, nd, coef + (size_t)i * NP, xref);
+                u[i] = fmin(fmax(v, 0.0), O->U_M);
+            }
+            orc_game_dynamics(P, p, u, g);
+            for (int s = 0; s < J; ++s) {
+                p[s] += O->h * g[s];
+                p_path[((size_t)k * (T + 1) + (size_t)t + 1) * J + s] = p[s];
+                if (u_path) u_path[((size_t)k * T + (size_t)t) * J + s] = u[s];
+            }
+        }
+    }
+    free(coef);
 }

@@ -88,6 +88,8 @@ def _declare(L):
                                  _dp, C.POINTER(C.c_long), _dp, _dp]
     L.orc_game_solve.restype = C.c_int
     L.orc_game_lq.argtypes = [C.POINTER(GameParams), C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.orc_game_paths.argtypes = [C.POINTER(GameParams), C.POINTER(GameOpts), _dp, C.c_long, _dp, C.c_long, _dp,
+                                 _dp]
     if hasattr(L, "orc_mlp_forward"):
         _declare_mlp(L)
 
@@ -322,6 +324,20 @@ def game_lq(p, h: float, R: int):
     f = np.empty((R, J))
     lib().orc_game_lq(C.byref(P), float(h), int(R), _p(Q), _p(b), _p(a), _p(F), _p(f))
     return {"Q": Q, "b": b, "a": a, "F": F, "f": f}
+
+
+def game_paths(p, opts: GameOpts, u_nodal, p0, T: int):
+    """Time paths along the policy interpolated from the nodal controls: returns
+    (p_path [K, T+1, J], u_path [K, T, J])."""
+    P = make_params(p)
+    J = P.J
+    un = _f64(u_nodal).reshape(-1)
+    q0 = _f64(p0).reshape(-1, J)
+    K = q0.shape[0]
+    pp = np.empty((K, T + 1, J))
+    up = np.empty((K, T, J))
+    lib().orc_game_paths(C.byref(P), C.byref(opts), _p(un), int(K), _p(q0), int(T), _p(pp), _p(up))
+    return pp, up
 
 
 # ---- surrogate network (FP64) ----------------------------------------------

@@ -223,3 +223,26 @@ def test_diverging_warm_start_falls_back_to_cold(ctx):
     cb.game_solve(ctx, p, o, Vn=[Vn])
     Vg, ug, rg = cb.game_solve(ctx, p, o, V0=[Vn], u0=[uc[0]])
     assert rg[0].restarts == 0 and rg[0].iters <= 2
+
+
+@pytest.mark.parametrize("J,n,prec,pair,perm,tol", [
+    (2, 9, "fp64", (0, 1), (1, 0), 1e-12),
+    (3, 9, "fp64", (0, 2), (2, 1, 0), 1e-12),
+    (4, 5, "fp64", (2, 3), (0, 1, 3, 2), 1e-12),
+    (3, 17, "bf16x6", (0, 2), (2, 1, 0), 1e-6),
+    (3, 33, "tf32x3", (0, 2), (2, 1, 0), 1e-6)])
+def test_symmetric_players_on_gpu(ctx, J, n, prec, pair, perm, tol):
+    """The symmetry invariants of Section 4's J = 2, 3, 4 examples on the converged
+    GPU solves: V_i(p) = V_k(sigma p), u_i(p) = u_k(sigma p) for the symmetric pair
+    (FP64 to rounding; the split forms to their error floor)."""
+    p = I.game_params(J)
+    Vn = [torch.empty((J, n ** J), dtype=torch.float64, device="cuda")]
+    _, u, res = cb.game_solve(ctx, p, cb.game_opts(n, tol=1e-10, max_iter=20000, prec=prec, polish_fp64=False),
+                              Vn=Vn, raise_on_error=False)
+    assert res[0].status in (0, 5)        # converged, or (split) stopped at its floor
+    shape = (J,) + (n,) * J
+    V = Vn[0].cpu().numpy().reshape(shape)
+    U = u[0].cpu().numpy().reshape(shape)
+    i, k = pair
+    assert np.abs(V[i] - np.transpose(V[k], perm)).max() <= tol * np.abs(V).max()
+    assert np.abs(U[i] - np.transpose(U[k], perm)).max() <= tol

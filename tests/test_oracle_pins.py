@@ -303,3 +303,76 @@ def test_game_node_update_matches_direct_maximisation():
             vals = np.array(vals)
             assert vs >= vals.max() - 1e-15
             assert abs(vs - vals.max()) < 2e-9      # grid step 1e-3: h (1e-3)^2 / 8 bound
+
+
+@pytest.mark.parametrize("J,n,pair,perm", [(2, 5, (0, 1), (1, 0)), (3, 5, (0, 2), (2, 1, 0)),
+                                           (4, 4, (2, 3), (0, 1, 3, 2))])
+def test_game_symmetric_players(J, n, pair, perm):
+    """Section 4's examples with identical player parameters: the two players of
+    the 2-player game, players 1 and 3 of the 3-player chain and players 3 and 4
+    of the 4-player configuration are symmetric, so V_i(p) = V_k(sigma p) and
+    u_i(p) = u_k(sigma p) with sigma the swap of coordinates i and k, iterate by
+    iterate (a wrong neighbour entry or a contraction over the wrong mode breaks
+    it)."""
+    p = I.game_params(J)
+    res = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=6))
+    shape = (J,) + (n,) * J
+    V, u = res["Vnod"].reshape(shape), res["u"].reshape(shape)
+    i, k = pair
+    assert np.abs(V[i] - np.transpose(V[k], perm)).max() <= 1e-12 * np.abs(V).max()
+    assert np.abs(u[i] - np.transpose(u[k], perm)).max() <= 1e-12
+    # and the pair is not trivially equal to a non-symmetric player
+    others = [q for q in range(J) if q not in pair]
+    if others:
+        assert np.abs(V[others[0]] - V[i]).max() > 1e-6 * np.abs(V).max()
+
+
+def test_game_paths_follow_affine_lq_policy():
+    """With no control bound active the equilibrium policy of the discrete game is
+    affine, u = F p + f (the closed-form LQ recursion). Its nodal values are
+    reproduced exactly by the interpolant, so the oracle's time path must equal
+    the affine recursion p_{t+1} = p_t + h ((K/m - diag c) p_t + beta (F p_t + f))
+    computed here with numpy. Domain P_M = 0.8: the steady state (about 0.5) is
+    inside it and the controls stay in (0.09, 0.45) on the whole box, and the
+    paths are checked to stay in it (outside, polynomial extrapolation multiplies
+    rounding-level coefficients by large T_k). Bound: the interpolant's rounding,
+    about J n^J ulp (<= 3e-13) per step, damped by the recursion (eigenvalues of
+    K/m - diag c + diag(beta) F at or below -0.8): <= 4e-11; 1e-10 asserted."""
+    for J in (2, 3, 4):
+        p = I.game_params(J)
+        h, P_M, n = 1e-2, 0.8, 5
+        lq = O.game_lq(p, h, 6000)
+        F, f = lq["F"][-1], lq["f"][-1]
+        opts = O.make_opts(n, h=h, P_M=P_M, U_M=1.0)
+        pb, _ = O.game_nodes(opts, J)
+        U = (pb @ F.T + f).T                       # J x n^J nodal controls
+        assert (U > 0).all() and (U < 1).all()
+        rng = np.random.default_rng(J)
+        p0 = rng.uniform(0, P_M, (3, J))
+        T = 600
+        pp, up = O.game_paths(p, opts, U, p0, T)
+        assert (pp >= 0).all() and (pp <= P_M).all()
+        M = p["K"] / p["m"] - np.diag(p["c"]) + np.diag(p["beta"]) @ F
+        q = p0.copy()
+        for t in range(T):
+            u = q @ F.T + f
+            assert np.abs(up[:, t] - u).max() < 1e-10
+            q = q + h * (q @ M.T + p["beta"] * f)
+            assert np.abs(pp[:, t + 1] - q).max() < 1e-10
+        # the path approaches the steady state -M^{-1} beta f
+        ps = -np.linalg.solve(M, p["beta"] * f)
+        assert np.abs(pp[:, -1] - ps).max() < np.abs(p0 - ps).max()
+
+
+def test_game_paths_of_symmetric_players_coincide():
+    """Players 1 and 3 of the 3-player chain are symmetric: from stocks with
+    p_1 = p_3 their emission and stock paths coincide (solved policy, bounds
+    active on part of the box)."""
+    p = I.game_params(3)
+    opts = O.make_opts(5, tol=0.0, max_iter=200)
+    r = O.game_solve(p, opts)
+    p0 = np.array([[0.1, 0.4, 0.1], [0.8, 0.2, 0.8], [0.0, 0.0, 0.0]])
+    pp, up = O.game_paths(p, opts, r["u"], p0, 400)
+    assert np.abs(pp[:, :, 0] - pp[:, :, 2]).max() < 1e-13
+    assert np.abs(up[:, :, 0] - up[:, :, 2]).max() < 1e-13
+    assert np.abs(pp[:, :, 0] - pp[:, :, 1]).max() > 1e-3
