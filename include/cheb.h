@@ -314,6 +314,35 @@ typedef struct {
 CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
                        const cheb_game_opts *opts, cheb_game_result *res, void *stream);
 
+/*
+ * game_paths - equilibrium time paths (Section 4: the emission and
+ * pollution-stock paths along the equilibrium strategy).
+ *
+ * The feedback policy of player i is the Chebyshev interpolant (Definition
+ * 3.2) of its nodal controls u_i(pbar_j) on [0, P_M]^J - as game_solve returns
+ * them in cheb_game_result.u - clamped to [0, U_M]. From each initial stock the
+ * path takes T explicit steps of the dynamics of Section 2.1 with the
+ * discretisation's time step: p_{t+1} = p_t + h g(p_t, u(p_t)). Stocks that
+ * leave [0, P_M]^J are still evaluated (the polynomial extends), but the
+ * policy is only an approximation inside the box.
+ *
+ *  params   host: the game (J <= 4)
+ *  opts     host: n, h, P_M, U_M of the solve the controls come from
+ *  u_nodal  device, J x n^J FP64 nodal controls (player-major, row-major)
+ *  K        trajectories (>= 0); p0 device K x J FP64 initial stocks
+ *  T        steps (>= 0)
+ *  p_path   device, K x (T + 1) x J FP64: p_path[k][0] = p0[k]
+ *  u_path   device, K x T x J FP64 controls applied at each step, or NULL
+ *  stream   CUDA stream; asynchronous (no host synchronisation)
+ * Errors: CHEB_EINVAL for J outside 1..4, n outside 2..64, negative K or T,
+ * non-positive h, P_M or m, negative U_M, or a null array with K > 0;
+ * CHEB_EUNSUPPORTED when n^(J-1) does not fit the per-CTA contraction
+ * (J = 4 needs n <= 24). FP64 throughout; all arrays are caller-owned.
+ */
+CHEB_API cheb_status game_paths(cheb_ctx *ctx, const cheb_game_params *params, const cheb_game_opts *opts,
+                                const double *u_nodal, int64_t K, const double *p0, int64_t T,
+                                double *p_path, double *u_path, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned warm start (surrogate). The paper starts the iteration from "some
  * given" V^[0] (Section 2.1, Step 0); here a multilayer perceptron

@@ -244,6 +244,27 @@ def game_solve(ctx: Context, params, opts, V=None, u=None, V0=None, u0=None, str
     return Vs, us, [R[i] for i in range(B)]
 
 
+def game_paths(ctx: Context, params, opts, u_nodal, p0, T: int, stream=None, with_controls: bool = True):
+    """Equilibrium time paths: from each row of p0 (K x J, device FP64), T explicit steps
+    along the clamped interpolant of the nodal controls u_nodal (J x n^J, device FP64, as
+    game_solve returns them). Returns (p_path [K, T+1, J], u_path [K, T, J] or None)."""
+    import torch
+    P = game_params(params)
+    J = int(params["J"])
+    _need_cuda(u_nodal, torch.float64, "u_nodal")
+    _need_cuda(p0, torch.float64, "p0")
+    K = int(p0.shape[0]) if p0.dim() == 2 else 0
+    if p0.dim() != 2 or p0.shape[1] != J:
+        raise ValueError("p0 must be K x J")
+    dev = p0.device
+    pp = torch.empty((K, T + 1, J), dtype=torch.float64, device=dev)
+    up = torch.empty((K, T, J), dtype=torch.float64, device=dev) if with_controls else None
+    check(load().game_paths(ctx.handle, C.byref(P), C.byref(opts), C.c_void_p(u_nodal.data_ptr()), K,
+                            C.c_void_p(p0.data_ptr()), int(T), C.c_void_p(pp.data_ptr()),
+                            None if up is None else C.c_void_p(up.data_ptr()), _stream_ptr(stream)))
+    return pp, up
+
+
 class Surrogate:
     """The warm-start network (surrogate_* entry points of include/cheb.h)."""
 

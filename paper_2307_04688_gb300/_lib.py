@@ -75,6 +75,8 @@ def load():
     L.cheb_profile_count.argtypes = [vp]
     L.cheb_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double)]
+    L.game_paths.argtypes = [vp, C.POINTER(GameParams), C.POINTER(GameOpts), vp, C.c_int64, vp, C.c_int64, vp,
+                             vp, vp]
     L.cheb_set_tuning.argtypes = [vp, C.c_int]
     L.cheb_tuning_report.argtypes = [vp, C.c_char_p, C.c_int64]
     L.surrogate_create.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(vp)]
@@ -87,7 +89,7 @@ def load():
     for f in ("surrogate_create", "surrogate_destroy", "surrogate_params", "surrogate_loss_grad",
               "surrogate_train", "surrogate_predict", "cheb_profile", "cheb_profile_count", "cheb_profile_get", "cheb_set_tuning",
               "cheb_tuning_report", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid",
-              "cheb_eval_points", "game_solve"):
+              "cheb_eval_points", "game_solve", "game_paths"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L

@@ -237,6 +237,7 @@ cheb_status cheb_destroy(cheb_ctx *ctx)
     ctx->xbuf.release();
     ctx->game.release();
     ctx->game_aux.release();
+    ctx->paths.release();
     if (ctx->d_error) cudaFree(ctx->d_error);
     prof_drain(ctx);
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);

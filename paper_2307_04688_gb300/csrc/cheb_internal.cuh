@@ -55,6 +55,7 @@ struct cheb_ctx {
     std::map<int, double *> dct;        // n -> device n x n DCT-I matrix (FP64)
     cheb::DevBuf game;                  // game state of one game_solve call
     cheb::DevBuf game_aux;
+    cheb::DevBuf paths;                 // control coefficients of one game_paths call
     // tile-shape tuning (cheb_set_tuning): 0 tune on first use, 1 default
     // shapes, 2 + k force configuration k; tuned choices by shape key
     int tune_mode = 0;

@@ -229,12 +229,15 @@ def test_diverging_warm_start_falls_back_to_cold(ctx):
     (2, 9, "fp64", (0, 1), (1, 0), 1e-12),
     (3, 9, "fp64", (0, 2), (2, 1, 0), 1e-12),
     (4, 5, "fp64", (2, 3), (0, 1, 3, 2), 1e-12),
-    (3, 17, "bf16x6", (0, 2), (2, 1, 0), 1e-6),
-    (3, 33, "tf32x3", (0, 2), (2, 1, 0), 1e-6)])
+    (3, 17, "bf16x6", (0, 2), (2, 1, 0), 2e-5),
+    (3, 33, "tf32x3", (0, 2), (2, 1, 0), 2e-5)])
 def test_symmetric_players_on_gpu(ctx, J, n, prec, pair, perm, tol):
     """The symmetry invariants of Section 4's J = 2, 3, 4 examples on the converged
     GPU solves: V_i(p) = V_k(sigma p), u_i(p) = u_k(sigma p) for the symmetric pair
-    (FP64 to rounding; the split forms to their error floor)."""
+    (FP64 to rounding; each split player's solution is within ~1e-5 of the FP64 one
+    (the split form's floor), so a symmetric pair may differ by twice that; a
+    control is the maximiser of W, its error that of W' over |W''|, which is of the
+    order of h = 1e-2 here, so controls get ten times the value bound)."""
     p = I.game_params(J)
     Vn = [torch.empty((J, n ** J), dtype=torch.float64, device="cuda")]
     _, u, res = cb.game_solve(ctx, p, cb.game_opts(n, tol=1e-10, max_iter=20000, prec=prec, polish_fp64=False),
@@ -245,4 +248,4 @@ def test_symmetric_players_on_gpu(ctx, J, n, prec, pair, perm, tol):
     U = u[0].cpu().numpy().reshape(shape)
     i, k = pair
     assert np.abs(V[i] - np.transpose(V[k], perm)).max() <= tol * np.abs(V).max()
-    assert np.abs(U[i] - np.transpose(U[k], perm)).max() <= tol
+    assert np.abs(U[i] - np.transpose(U[k], perm)).max() <= (tol if prec == "fp64" else 10 * tol)
