@@ -7,11 +7,12 @@
 // every mode and leaves the modes in their original order.
 //
 // Design (GB300):
-//  - persistent CTAs of 256 threads (8 warps), two CTAs per SM; a CTA owns a
-//    128-row tile of X at a time;
+//  - persistent CTAs of 256 threads (8 warps), up to four per SM (shared
+//    memory decides); a CTA owns a 128-row tile at a time;
 //  - the X tile is one contiguous block of global memory, copied to shared
-//    memory by the TMA engine (cp.async.bulk, completion on an mbarrier) one
-//    tile ahead of its use (double buffer);
+//    memory by the TMA engine (cp.async.bulk, completion on an mbarrier) into
+//    one staging slot that is refilled with the next tile as soon as the
+//    current one is split, so the copy overlaps the MMA and the epilogue;
 //  - two threads per row split the row into S_A BF16 (or TF32) parts in FP32
 //    arithmetic (FP64 inputs are rounded to FP32 first: GB300's FP64 pipe is
 //    far too slow for this) and write them in the no-swizzle K-major
@@ -39,6 +40,10 @@ using namespace tc;
 
 constexpr int kTileM = 128;
 constexpr int kThreads = 256;
+// X staging slots. One slot, refilled as soon as the tile in it is split (its
+// copy then overlaps the tile's MMA and epilogue), keeps shared memory small
+// enough for four CTAs per SM at BF16x6 (three with FP64 rows).
+constexpr int kStages = 1;
 constexpr int kMaxTail = 2;   // K columns beyond the last full instruction K done in FP32
 constexpr int kMaxM = 256;
 
@@ -147,7 +152,7 @@ modeprod_tc_kernel(const Params P)
     uint8_t *sB = sA + SA * a_split_bytes;                // SB x [Np x Kp]
     float *sBt = reinterpret_cast<float *>(sB + SB * b_split_bytes);   // kMaxTail x Np FP32 tail columns of B
     uint8_t *sX = reinterpret_cast<uint8_t *>(sBt + kMaxTail * kMaxM);  // 2 x staged X tile
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sX + 2 * stage_bytes);  // [0,1] loads, [2] mma
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sX + kStages * stage_bytes);  // [0,1] loads, [2] mma
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -257,9 +262,9 @@ modeprod_tc_kernel(const Params P)
     const int ehalf = warp >> 2;            // epilogue: column-chunk parity
     int it = 0;
     for (; tile < ntiles; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
+        const int buf = kStages == 2 ? (it & 1) : 0;
         const int64_t next = tile + gridDim.x;
-        if (next < ntiles && tile_full(next)) {
+        if (kStages == 2 && next < ntiles && tile_full(next)) {
             if (tid == 0) issue_load(next, buf ^ 1);
             load_pending |= 1u << (buf ^ 1);
         }
@@ -308,6 +313,11 @@ modeprod_tc_kernel(const Params P)
         __syncthreads();
         tc_fence_after();
         if (*abort_flag) break;
+        // one slot: the rows are split, so the next tile's copy can start now
+        if (kStages == 1 && next < ntiles && tile_full(next)) {
+            if (tid == 0) issue_load(next, 0);
+            load_pending |= 1u;
+        }
         if (tid == 0) {
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
@@ -409,7 +419,7 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
     const size_t a_bytes = (size_t)F::SA * kTileM * P.Kp * F::EBYTES;
     const size_t b_bytes = (size_t)F::SB * P.Np * P.Kp * F::EBYTES;
     const size_t stage = (size_t)round_up(kTileM * P.n * (int)sizeof(XT), 128);
-    const size_t smem = a_bytes + b_bytes + kMaxTail * kMaxM * sizeof(float) + 2 * stage + 64;
+    const size_t smem = a_bytes + b_bytes + kMaxTail * kMaxM * sizeof(float) + kStages * stage + 64;
     if (smem > 227 * 1024) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: tile does not fit in shared memory");
     auto kern = modeprod_tc_kernel<FORM, XT>;
     static bool attr_done = false;
