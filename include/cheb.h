@@ -57,12 +57,19 @@ typedef enum {
  *               same three products, FP32 accumulation.
  *  CHEB_BF16X6  three-way BF16 split x = x0 + x1 + x2, the six products with
  *               i + j <= 2, FP32 accumulation.
+ *  CHEB_DF64    double-float: every value a pair of FP32 numbers (about 48
+ *               significant bits), error-free products and compensated sums on
+ *               the FP32 pipe (GB300's FP64 pipe is ~1.25 TFLOP/s); relative
+ *               errors of a few 1e-14. game_solve only (its player update; the
+ *               refit and the residual stay FP64); the other calls return
+ *               CHEB_EINVAL for it.
  * The split forms return FP32 results. */
 typedef enum {
     CHEB_FP64 = 0,
     CHEB_TF32X3 = 1,
     CHEB_BF16X3 = 2,
-    CHEB_BF16X6 = 3
+    CHEB_BF16X6 = 3,
+    CHEB_DF64 = 4
 } cheb_precision;
 
 typedef struct cheb_ctx cheb_ctx;
@@ -267,8 +274,10 @@ typedef struct {
                            maximisation runs on the exact one-variable polynomial */
     int64_t max_iter;   /* iteration cap (CHEB_ENOCONV when reached) */
     int32_t prec;       /* cheb_precision of the evaluation products */
-    int32_t polish_fp64;/* split forms: 1 = continue in FP64 once the split
-                           iteration stagnates, so that tol is reached in FP64 */
+    int32_t polish_fp64;/* split forms: once the split iteration stagnates, 1 =
+                           continue with FP64-level accuracy in double-float
+                           (the CHEB_DF64 update), 2 = continue on the FP64 pipe
+                           (the CHEB_FP64 update); 0 = stop there (CHEB_ESTALL) */
 } cheb_game_opts;
 
 typedef struct {

@@ -202,12 +202,14 @@ def game_params(p) -> GameParams:
 
 
 def game_opts(n: int, h: float = 1e-2, P_M: float = 1.0, U_M: float = 1.0, tol: float = 1e-10,
-              max_iter: int = 100000, prec="fp64", polish_fp64: bool = True, n_u: int = 0) -> GameOpts:
+              max_iter: int = 100000, prec="fp64", polish_fp64=True, n_u: int = 0) -> GameOpts:
+    """polish_fp64 (split forms, once the split iteration stagnates): True or 1 continue in
+    double-float (FP64-level accuracy on the FP32 pipe), 2 on the FP64 pipe, False stop."""
     o = GameOpts()
     o.h, o.P_M, o.U_M, o.tol = float(h), float(P_M), float(U_M), float(tol)
     o.n, o.n_u, o.max_iter = int(n), int(n_u), int(max_iter)
     o.prec = precision(prec)
-    o.polish_fp64 = int(bool(polish_fp64))
+    o.polish_fp64 = 2 if polish_fp64 == 2 else int(bool(polish_fp64))
     return o
 
 

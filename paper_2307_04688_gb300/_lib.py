@@ -17,7 +17,9 @@ CHEB_OK, CHEB_EINVAL, CHEB_ENOMEM, CHEB_ECUDA, CHEB_ENOCONV, CHEB_ESTALL, CHEB_E
 STATUS_NAMES = {0: "CHEB_OK", 1: "CHEB_EINVAL", 2: "CHEB_ENOMEM", 3: "CHEB_ECUDA", 4: "CHEB_ENOCONV",
                 5: "CHEB_ESTALL", 6: "CHEB_ETIMEOUT", 7: "CHEB_EUNSUPPORTED"}
 CHEB_FP64, CHEB_TF32X3, CHEB_BF16X3, CHEB_BF16X6 = range(4)
-PRECISIONS = {"fp64": CHEB_FP64, "tf32x3": CHEB_TF32X3, "bf16x3": CHEB_BF16X3, "bf16x6": CHEB_BF16X6}
+CHEB_DF64 = 4
+PRECISIONS = {"fp64": CHEB_FP64, "tf32x3": CHEB_TF32X3, "bf16x3": CHEB_BF16X3, "bf16x6": CHEB_BF16X6,
+              "df64": CHEB_DF64}
 
 
 class ChebError(RuntimeError):

@@ -16,10 +16,11 @@
 // enqueued in chunks captured once into a CUDA graph; the host only reads the
 // per-instance status between chunks.
 //
-// Two evaluation kernels exist: FP64 on the CUDA cores (player_f64_kernel)
-// and the split-precision tensor-core kernel (game_tc.cu). A device-side
-// mode flag per instance selects one of them each iteration, so the switch
-// from split to FP64 iterations (polish) needs no host round trip.
+// Three evaluation kernels exist: FP64 on the CUDA cores (player_f64_kernel),
+// double-float on the FP32 pipe (game_df.cu) and the split-precision
+// tensor-core kernel (game_tc.cu). A device-side mode flag per instance
+// selects one of them each iteration, so the switch from split to
+// FP64-accurate iterations (polish) needs no host round trip.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -190,7 +191,7 @@ __global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *
         s.status = CHEB_ENOCONV;
     } else if (s.since_best > g.stall_window) {
         if (s.mode == 1 && g.polish) {
-            s.mode = 0;                 // continue in FP64
+            s.mode = g.polish_mode;     // continue with FP64 accuracy (double-float or FP64)
             s.since_best = 0;
             s.best_res = res;
         } else {
@@ -275,8 +276,9 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     const size_t tc_bytes = game_tc_workspace_bytes(J, n, NP, B, prec);
     size_t bytes = 0;
     auto rnd = [](size_t x) { return (x + 255) & ~size_t(255); };
-    bytes += 9 * rnd(arr) + rnd(sizeof(double) * 64) + rnd(sizeof(GameDev) * B) + rnd(sizeof(GameStat) * B) +
-             rnd(tc_bytes);
+    const bool any_df = prec == CHEB_DF64 || (prec != CHEB_FP64 && opts[members[0]].polish_fp64 == 1);
+    bytes += 9 * rnd(arr) + (any_df ? rnd(arr) : 0) + rnd(sizeof(double) * 64) + rnd(sizeof(GameDev) * B) +
+             rnd(sizeof(GameStat) * B) + rnd(tc_bytes);
     cheb_status r = ctx->game.reserve(bytes);
     if (r) return r;
     uint8_t *base = static_cast<uint8_t *>(ctx->game.ptr);
@@ -299,6 +301,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     GameDev *d_inst = reinterpret_cast<GameDev *>(take(sizeof(GameDev) * B));
     GameStat *d_stat = reinterpret_cast<GameStat *>(take(sizeof(GameStat) * B));
     uint8_t *tc_ws = take(tc_bytes);
+    float *Cdf_all = any_df ? reinterpret_cast<float *>(take(arr)) : nullptr;   // (hi, lo) per coefficient
     (void)init;
 
     // nodes cos(pi k / N) (the integer argument is exact)
@@ -334,6 +337,8 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         g.tol = o.tol;
         g.max_iter = o.max_iter;
         g.polish = o.polish_fp64 != 0;
+        g.polish_mode = o.polish_fp64 == 2 ? 0 : 2;
+        g.Cdf = Cdf_all ? Cdf_all + 2 * per * q : nullptr;
         g.stall_window = 200;
         g.C = C_all + per * q;
         g.u = u_all + per * q;
@@ -351,7 +356,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         std::memset(&s, 0, sizeof(s));
         s.best_res = INFINITY;
         s.last_res = INFINITY;
-        s.mode = prec == CHEB_FP64 ? 0 : 1;
+        s.mode = prec == CHEB_FP64 ? 0 : prec == CHEB_DF64 ? 2 : 1;
         s.mode_initial = s.mode;
         s.warm = (res[b].V0 != nullptr || res[b].u0 != nullptr) ? 1 : 0;
         s.status = CHEB_ENOCONV;
@@ -379,10 +384,14 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
             next_state_kernel<<<dim3(node_blocks, B), 128, 0, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
-        if (prec != CHEB_FP64) {
+        const bool split = prec != CHEB_FP64 && prec != CHEB_DF64;
+        if (split) {
             if ((e = game_tc_player(ctx, d_inst, d_stat, hinst.data(), B, J, n, NP, prec, tc_ws, s))) return e;
         }
-        if (prec == CHEB_FP64 || hinst[0].polish) {
+        if (prec == CHEB_DF64 || (split && hinst[0].polish && hinst[0].polish_mode == 2)) {
+            if ((e = game_df_player(d_inst, d_stat, B, J, NP, s))) return e;
+        }
+        if (prec == CHEB_FP64 || (split && hinst[0].polish && hinst[0].polish_mode == 0)) {
             ProfScope prof("game_player_f64", s);
             player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
         }
@@ -398,7 +407,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     };
 
     // ---- tile shapes of the split player update, timed on this group ----
-    if (prec != CHEB_FP64) {
+    if (prec != CHEB_FP64 && prec != CHEB_DF64) {
         next_state_kernel<<<dim3(node_blocks, B), 128, 0, st>>>(d_inst, d_stat);
         CHEB_CUDA_TRY(cudaGetLastError());
         if ((r = game_tc_tune(ctx, d_inst, d_stat, B, J, n, prec, st))) return r;
@@ -538,8 +547,10 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
             !(o.tol >= 0) || o.max_iter < 1)
             return fail(CHEB_EINVAL,
                         "game_solve: need h, rho, P_M, U_M, m > 0, rho h < 1, tol >= 0, max_iter >= 1");
-        if (o.prec < CHEB_FP64 || o.prec > CHEB_BF16X6) return fail(CHEB_EINVAL, "game_solve: bad precision");
-        if (o.prec != CHEB_FP64 && (p.J != 3 || (o.n != 5 && o.n != 9 && o.n != 17 && o.n != 33)))
+        if (o.prec < CHEB_FP64 || o.prec > CHEB_DF64) return fail(CHEB_EINVAL, "game_solve: bad precision");
+        if (o.polish_fp64 < 0 || o.polish_fp64 > 2) return fail(CHEB_EINVAL, "game_solve: polish_fp64 must be 0, 1 or 2");
+        if (o.prec != CHEB_FP64 && o.prec != CHEB_DF64 &&
+            (p.J != 3 || (o.n != 5 && o.n != 9 && o.n != 17 && o.n != 33)))
             return fail(CHEB_EUNSUPPORTED, "game_solve: the split forms need J = 3 and n in {5, 9, 17, 33}");
         for (int t = 0; t < p.J * p.J; ++t)
             if (!std::isfinite(p.K[t])) return fail(CHEB_EINVAL, "game_solve: K not finite");

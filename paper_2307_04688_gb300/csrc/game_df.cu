@@ -1,0 +1,296 @@
+// Double-float player update of the game iteration (Section 3.4, Steps 1-3):
+// the FP64 player update carried out on GB300's FP32 pipe.
+//
+// GB300 runs FP64 at about 1.25 TFLOP/s, two orders of magnitude below its
+// FP32 rate, and the FP64 player update is its slowest stage (n^J FMAs per
+// node and player for the series, and a Newton search per node). Here every
+// value is a pair of FP32 numbers hi + lo (about 48 significant bits):
+// products are error-free (hi*hi exact by fma, plus the cross terms), sums
+// compensated (two-sum), so the series w_j[k] and the value at the maximiser
+// carry relative errors of a few 1e-14 while using FP32 instructions only.
+//  - coefficients: split once per iteration into (hi, lo) pairs by
+//    game_coef_df_kernel (the refit itself stays FP64);
+//  - T_k of the next states by the three-term recurrence in double-float;
+//  - the contraction as in the FP64 kernel (last mode innermost), each inner
+//    dot product accumulated unnormalised (the rounding errors of the sums
+//    and products collected in the low word), renormalised once per dot;
+//  - Step 3: projected Newton in FP32 from the previous control, then two
+//    double-float Newton steps at a concave interior point (the control must
+//    be accurate to about 1e-13: it moves the other players' next states);
+//    as in the FP64 update the Newton point and the two bounds compete, their
+//    values in double-float. The residual is FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "game_internal.cuh"
+
+namespace cheb {
+namespace game {
+namespace {
+
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_of(double x)
+{
+    dfl r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ double df_val(dfl a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dfl df_norm(float s, float e)
+{
+    dfl r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    return df_norm(s, e);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+
+__device__ __forceinline__ dfl df_scale(dfl a, float s) { return {a.hi * s, a.lo * s}; }   // s a power of two
+
+// Running sum of products: hi is the plain FP32 sum, lo collects the rounding
+// error of every sum and product (renormalised by the caller).
+struct dacc {
+    float hi = 0.0f, lo = 0.0f;
+};
+
+__device__ __forceinline__ void df_mac(dacc &acc, dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    const float s = acc.hi + p, bb = s - acc.hi;
+    acc.lo += ((acc.hi - (s - bb)) + (p - bb)) + pe;
+    acc.hi = s;
+}
+
+__device__ __forceinline__ dfl df_done(const dacc &a) { return df_norm(a.hi, a.lo); }
+
+// T_0..T_{n-1}(x) in double-float by the three-term recurrence (valid for any x)
+__device__ __forceinline__ void df_row(int n, double x, dfl *T)
+{
+    const dfl xf = df_of(x);
+    T[0] = {1.0f, 0.0f};
+    if (n > 1) T[1] = xf;
+    for (int k = 2; k < n; ++k) T[k] = df_add(df_scale(df_mul(xf, T[k - 1]), 2.0f), df_neg(T[k - 2]));
+}
+
+// The Bellman objective along the next states as a function of the player's
+// own control, W(u) = h (u (A - u/2) - phi pbar^2 / 2) + delta sum_m w_m T_m(x),
+// x = xc + slope u, in FP32 with its first two derivatives (the Newton search).
+__device__ __forceinline__ void objective_f32(const float *w, int n, float xc, float slope, float hA, float h,
+                                              float delta, float u, float &W, float &W1, float &W2)
+{
+    const float x = xc + slope * u;
+    float t0 = 1.0f, t1 = x, d0 = 0.0f, d1 = 1.0f, e0 = 0.0f, e1 = 0.0f;
+    float s = w[0] + (n > 1 ? w[1] * x : 0.0f), s1 = n > 1 ? w[1] : 0.0f, s2 = 0.0f;
+    for (int m = 2; m < n; ++m) {
+        const float t2 = 2.0f * x * t1 - t0;
+        const float d2 = 2.0f * t1 + 2.0f * x * d1 - d0;
+        const float e2 = 4.0f * d1 + 2.0f * x * e1 - e0;
+        s = fmaf(w[m], t2, s);
+        s1 = fmaf(w[m], d2, s1);
+        s2 = fmaf(w[m], e2, s2);
+        t0 = t1; t1 = t2;
+        d0 = d1; d1 = d2;
+        e0 = e1; e1 = e2;
+    }
+    W = hA * u - 0.5f * h * u * u + delta * s;
+    W1 = hA - h * u + delta * slope * s1;
+    W2 = -h + delta * slope * slope * s2;
+}
+
+// sum_m w_m T_m(x) and sum_m w_m T'_m(x) in double-float (T' by differentiating
+// the recurrence: T'_m = 2 T_{m-1} + 2 x T'_{m-1} - T'_{m-2})
+__device__ __forceinline__ void series_df(const dfl *w, int n, dfl x, dfl &S, dfl &S1)
+{
+    dfl t0 = {1.0f, 0.0f}, t1 = x, d0 = {0.0f, 0.0f}, d1 = {1.0f, 0.0f};
+    dacc s, s1;
+    df_mac(s, w[0], t0);
+    if (n > 1) {
+        df_mac(s, w[1], t1);
+        df_mac(s1, w[1], d1);
+    }
+    for (int m = 2; m < n; ++m) {
+        const dfl t2 = df_add(df_scale(df_mul(x, t1), 2.0f), df_neg(t0));
+        const dfl d2 = df_add(df_add(df_scale(t1, 2.0f), df_scale(df_mul(x, d1), 2.0f)), df_neg(d0));
+        df_mac(s, w[m], t2);
+        df_mac(s1, w[m], d2);
+        t0 = t1; t1 = t2;
+        d0 = d1; d1 = d2;
+    }
+    S = df_done(s);
+    S1 = df_done(s1);
+}
+
+__global__ void game_coef_df_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats)
+{
+    if (stats[blockIdx.y].done || stats[blockIdx.y].mode != 2) return;
+    const GameDev g = insts[blockIdx.y];
+    const int total = g.J * g.NP;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const dfl c = df_of(g.C[t]);
+        g.Cdf[2 * t] = c.hi;
+        g.Cdf[2 * t + 1] = c.lo;
+    }
+}
+
+// One thread per (node, player), as the FP64 kernel.
+__global__ void __launch_bounds__(128)
+game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats)
+{
+    const int inst = blockIdx.z, i = blockIdx.y;
+    GameStat *st = &stats[inst];
+    if (st->done || st->mode != 2) return;
+    const GameDev g = insts[inst];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.NP) return;
+    const int J = g.J, n = g.n, NP = g.NP;
+    int stride[4];
+    stride[J - 1] = 1;
+    for (int s = J - 2; s >= 0; --s) stride[s] = stride[s + 1] * n;
+    int other[3], no = 0;
+    for (int s = 0; s < J; ++s)
+        if (s != i) other[no++] = s;
+    dfl T[3][kGameNMax];
+    for (int q = 0; q < no; ++q) df_row(n, g.X[other[q] * NP + j], T[q]);
+    const float2 *C = reinterpret_cast<const float2 *>(g.Cdf) + (size_t)i * NP;
+    auto coef = [&](size_t idx) {
+        const float2 v = __ldg(C + idx);
+        return dfl{v.x, v.y};
+    };
+    dfl w[kGameNMax];
+    for (int k = 0; k < n; ++k) {
+        const size_t ck = (size_t)k * stride[i];
+        if (no == 0) {
+            w[k] = coef(ck);
+        } else if (no == 1) {
+            dacc acc;
+            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride[other[0]]), T[0][a]);
+            w[k] = df_done(acc);
+        } else if (no == 2) {
+            dacc acc;
+            for (int a = 0; a < n; ++a) {
+                dacc t;
+                const size_t ca = ck + (size_t)a * stride[other[0]];
+                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride[other[1]]), T[1][b]);
+                df_mac(acc, df_done(t), T[0][a]);
+            }
+            w[k] = df_done(acc);
+        } else {
+            dacc acc;
+            for (int a = 0; a < n; ++a) {
+                dacc ta;
+                for (int b = 0; b < n; ++b) {
+                    dacc t;
+                    const size_t cab = ck + (size_t)a * stride[other[0]] + (size_t)b * stride[other[1]];
+                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride[other[2]]), T[2][c]);
+                    df_mac(ta, df_done(t), T[1][b]);
+                }
+                df_mac(acc, df_done(ta), T[0][a]);
+            }
+            w[k] = df_done(acc);
+        }
+    }
+    // Step 3
+    double xr[4], pb[4];
+    node_coords(g, j, xr, pb);
+    const double ui = g.u[i * NP + j];
+    const double slope = 2.0 * g.h * g.beta[i] / g.P_M;
+    const double xc = g.X[i * NP + j] - slope * ui;
+    const double hA = g.h * g.A[i];
+    const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+    float wf[kGameNMax];
+    for (int k = 0; k < n; ++k) wf[k] = w[k].hi + w[k].lo;
+    const float U_M = (float)g.U_M;
+    float u = fminf(fmaxf((float)ui, 0.0f), U_M);
+    float W, W1, W2;
+    for (int it = 0; it < 30; ++it) {
+        objective_f32(wf, n, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+        float un = (W2 < 0.0f) ? u - W1 / W2 : (W1 > 0.0f ? 0.5f * (u + U_M) : 0.5f * u);
+        un = fminf(fmaxf(un, 0.0f), U_M);
+        const float step = fabsf(un - u);
+        u = un;
+        if (step <= 1e-7f * U_M) break;
+    }
+    objective_f32(wf, n, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+    const dfl xcd = df_of(xc), sld = df_of(slope), hAd = df_of(hA), hd = df_of(g.h), dd = df_of(g.delta);
+    // W and W' at a control in double-float
+    auto value = [&](dfl uu, dfl *W1o) {
+        dfl S, S1;
+        series_df(w, n, df_add(xcd, df_mul(sld, uu)), S, S1);
+        const dfl hu = df_mul(hd, uu);
+        if (W1o) *W1o = df_add(df_add(hAd, df_neg(hu)), df_mul(df_mul(dd, sld), S1));
+        // h A u - h u^2 / 2 + delta S (+ hG0, added in FP64)
+        return df_add(df_add(df_mul(hAd, uu), df_neg(df_scale(df_mul(hu, uu), 0.5f))), df_mul(dd, S));
+    };
+    // a concave interior Newton point is refined by two Newton steps in
+    // double-float on W' (W'' from FP32 suffices for the step); then, as in
+    // the FP64 update, the bounds and the Newton point compete, ties to the
+    // smaller control
+    dfl ud = df_of((double)u);
+    if (u > 0.0f && u < U_M && W2 < 0.0f) {
+        for (int it = 0; it < 2; ++it) {
+            dfl W1d;
+            value(ud, &W1d);
+            ud = df_add(ud, df_of(-df_val(W1d) / (double)W2));
+        }
+    }
+    double us = fmin(fmax(df_val(ud), 0.0), g.U_M);
+    double bu = 0.0, V = df_val(value(dfl{0.0f, 0.0f}, nullptr)) + hG0;
+    {
+        const double vn = df_val(value(df_of(us), nullptr)) + hG0;
+        if (vn > V) { V = vn; bu = us; }
+        const double vm = df_val(value(df_of(g.U_M), nullptr)) + hG0;
+        if (vm > V) { V = vm; bu = g.U_M; }
+    }
+    us = bu;
+    us = fmin(fmax(us, 0.0), g.U_M);
+    g.u_new[i * NP + j] = us;
+    g.Vn_new[i * NP + j] = V;
+    const double d = fabs(V - g.Vn[i * NP + j]);
+    atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
+}
+
+}  // namespace
+
+cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st)
+{
+    const unsigned copy_blocks = (unsigned)std::min<int64_t>(((int64_t)J * NP + 255) / 256, 256);
+    {
+        ProfScope prof("game_coef_df", st);
+        game_coef_df_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, d_stat);
+        CHEB_CUDA_TRY(cudaGetLastError());
+    }
+    const unsigned node_blocks = (unsigned)((NP + 127) / 128);
+    ProfScope prof("game_player_df", st);
+    game_player_df_kernel<<<dim3(node_blocks, J, B), 128, 0, st>>>(d_inst, d_stat);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+}  // namespace game
+}  // namespace cheb

@@ -27,12 +27,15 @@ struct GameDev {
     const double *V0, *u0;        // optional initial nodal values / controls
     // split-precision path (game_tc.cu)
     void *bsplit;                 // pre-split coefficient operands, J x chunks
+    // double-float path (game_df.cu)
+    float *Cdf;                   // J x NP coefficient pairs (hi, lo)
+    int polish_mode;              // mode a stalled split iteration continues in (0 FP64, 2 double-float)
 };
 
 // One instance's progress, written by the commit kernel.
 struct GameStat {
     int done;
-    int mode;                     // 0: FP64 evaluation, 1: split precision
+    int mode;                     // 0: FP64 evaluation, 1: split precision, 2: double-float
     int mode_initial;             // the mode a (re)start begins in
     int status;                   // cheb_status once done
     int since_best;
@@ -142,6 +145,9 @@ __device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, in
 cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std::vector<int> &members,
                         const cheb_game_params *params, const cheb_game_opts *opts, cheb_game_result *res,
                         cudaStream_t st);
+
+// ---- double-float player update (game_df.cu): coefficient split + update ----
+cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st);
 
 // ---- split-precision player update (game_tc.cu) ----
 size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec);

@@ -249,3 +249,45 @@ def test_symmetric_players_on_gpu(ctx, J, n, prec, pair, perm, tol):
     i, k = pair
     assert np.abs(V[i] - np.transpose(V[k], perm)).max() <= tol * np.abs(V).max()
     assert np.abs(U[i] - np.transpose(U[k], perm)).max() <= (tol if prec == "fp64" else 10 * tol)
+
+
+@pytest.mark.parametrize("J,n,R", [(3, 5, 7), (2, 5, 40), (4, 4, 5), (3, 9, 3), (1, 6, 10)])
+def test_df64_iterations_match_oracle(ctx, J, n, R):
+    """CHEB_DF64: the player update in double-float (FP32 pairs, error-free products,
+    compensated sums). Per value a relative error of about n^2 2^-48 (< 1e-13 here),
+    carried through R contracting iterations: 1e-10 on coefficients and controls."""
+    p = I.draw_game_params(I.SplitMix64(10 + J * 7 + n), J)
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(n, tol=0.0, max_iter=R, prec="df64"), raise_on_error=False)
+    assert res[0].iters == R
+    ref = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=R))
+    assert rel(V[0].cpu().numpy(), ref["Vcoef"]) < 1e-10
+    assert np.abs(u[0].cpu().numpy() - ref["u"]).max() < 1e-10
+    assert abs(res[0].residual - ref["residual"]) <= 1e-10 * ref["residual"] + 1e-14
+
+
+def test_df64_full_size_tracks_fp64(ctx):
+    """n = 17, the +-30 % draw: 300 iterations in double-float and in FP64 from the same
+    cold start stay within 300 x ~1e-13 of each other; then the double-float solve
+    converges to 1e-10 like the FP64 one."""
+    p = I.single_game_workload()
+    R = 300
+    Vd, ud, rd = cb.game_solve(ctx, p, cb.game_opts(17, tol=0.0, max_iter=R, prec="df64"), raise_on_error=False)
+    Vf, uf, rf = cb.game_solve(ctx, p, cb.game_opts(17, tol=0.0, max_iter=R, prec="fp64"), raise_on_error=False)
+    assert rel(Vd[0].cpu().numpy(), Vf[0].cpu().numpy()) < 1e-9
+    assert (ud[0] - uf[0]).abs().max().item() < 1e-9
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(17, tol=1e-10, max_iter=20000, prec="df64"), raise_on_error=False)
+    assert res[0].status == 0 and res[0].residual < 1e-10
+
+
+@pytest.mark.parametrize("polish", [1, 2])
+def test_split_polish_modes_reach_tol(ctx, polish):
+    """A stalled split iteration continues in double-float (polish 1) or on the FP64 pipe
+    (polish 2); both reach tol = 1e-10 and the same solution (both within tol / (1 - delta)
+    of the fixed point)."""
+    p = I.single_game_workload()
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(9, tol=1e-10, max_iter=20000, prec="bf16x6", polish_fp64=polish),
+                              raise_on_error=False)
+    r = res[0]
+    assert r.status == 0 and r.residual < 1e-10 and r.iters > r.iters_split > 0
+    Vf, _, _ = cb.game_solve(ctx, p, cb.game_opts(9, tol=1e-10, max_iter=20000, prec="fp64"))
+    assert rel(V[0].cpu().numpy(), Vf[0].cpu().numpy()) < 1e-6
