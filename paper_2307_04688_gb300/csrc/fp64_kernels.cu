@@ -63,6 +63,23 @@ modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
     }
 }
 
+// The same product for small R (few tiles): one thread per output element, so
+// that the FP64 work spreads over the SMs instead of occupying a handful of
+// them (GB300's FP64 rate per SM is low). Same order of the k sum and the same
+// fma as the tiled kernel, hence bit-identical results.
+__global__ void modeprod_f64_small_kernel(const double *__restrict__ X, const double *__restrict__ B,
+                                          double *__restrict__ out, int64_t R, int n, int m)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * m) return;
+    const int j = (int)(t / R);
+    const int64_t r = t - (int64_t)j * R;
+    const double *xr = X + r * n, *bj = B + (int64_t)j * n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(__ldg(bj + k), __ldg(xr + k), acc);
+    out[t] = acc;
+}
+
 // T[j * n + l] = T_l(x~_j) by the three-term recurrence (valid off [-1,1]).
 __global__ void cheb_matrix_kernel(const double *__restrict__ x, int64_t stride, int64_t m, int n,
                                    double a, double b, double *__restrict__ T)
@@ -253,6 +270,14 @@ cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t 
     }
     const int64_t tiles = (R + kF64Rows - 1) / kF64Rows;
     if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many rows");
+    if (tiles * ((m + kF64Cols - 1) / kF64Cols) < 256 && R * m < (int64_t)1 << 26) {
+        ProfScope prof("modeprod_f64 R=" + std::to_string(R) + " n=" + std::to_string(n) +
+                           " m=" + std::to_string(m) + " (per element)",
+                       st);
+        modeprod_f64_small_kernel<<<(unsigned)((R * m + 127) / 128), 128, 0, st>>>(X, B, out, R, n, m);
+        CHEB_CUDA_TRY(cudaGetLastError());
+        return CHEB_OK;
+    }
     dim3 grid((unsigned)tiles, (unsigned)((m + kF64Cols - 1) / kF64Cols));
     if (grid.y > 65535) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many columns");
     ProfScope prof("modeprod_f64 R=" + std::to_string(R) + " n=" + std::to_string(n) +

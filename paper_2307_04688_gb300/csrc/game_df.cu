@@ -158,17 +158,26 @@ __global__ void game_coef_df_kernel(const GameDev *__restrict__ insts, const Gam
     }
 }
 
-// One thread per (node, player), as the FP64 kernel.
-__global__ void __launch_bounds__(128)
+// Eight threads per (node, player): thread g of a node forms w[k] for
+// k = g, g + 8, ..., the node's threads meet in shared memory and the first
+// one runs Step 3 (the serial dot products need many warps to hide their
+// latency; one thread per node leaves a few warps per SM).
+constexpr int kDfGroup = 8;
+constexpr int kDfNodes = 16;          // nodes per block of 128 threads
+
+__global__ void __launch_bounds__(kDfGroup * kDfNodes)
 game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats)
 {
+    __shared__ float2 w_sm[kDfNodes][kGameNMax];
     const int inst = blockIdx.z, i = blockIdx.y;
     GameStat *st = &stats[inst];
     if (st->done || st->mode != 2) return;
     const GameDev g = insts[inst];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.NP) return;
+    const int nl = threadIdx.x / kDfGroup, grp = threadIdx.x % kDfGroup;
+    const int j = blockIdx.x * kDfNodes + nl;
     const int J = g.J, n = g.n, NP = g.NP;
+    const bool valid = j < NP;
+    const int jc = valid ? j : NP - 1;
     int stride[4];
     stride[J - 1] = 1;
     for (int s = J - 2; s >= 0; --s) stride[s] = stride[s + 1] * n;
@@ -176,21 +185,21 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     for (int s = 0; s < J; ++s)
         if (s != i) other[no++] = s;
     dfl T[3][kGameNMax];
-    for (int q = 0; q < no; ++q) df_row(n, g.X[other[q] * NP + j], T[q]);
+    for (int q = 0; q < no; ++q) df_row(n, g.X[other[q] * NP + jc], T[q]);
     const float2 *C = reinterpret_cast<const float2 *>(g.Cdf) + (size_t)i * NP;
     auto coef = [&](size_t idx) {
         const float2 v = __ldg(C + idx);
         return dfl{v.x, v.y};
     };
-    dfl w[kGameNMax];
-    for (int k = 0; k < n; ++k) {
+    for (int k = grp; k < n; k += kDfGroup) {
         const size_t ck = (size_t)k * stride[i];
+        dfl wk;
         if (no == 0) {
-            w[k] = coef(ck);
+            wk = coef(ck);
         } else if (no == 1) {
             dacc acc;
             for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride[other[0]]), T[0][a]);
-            w[k] = df_done(acc);
+            wk = df_done(acc);
         } else if (no == 2) {
             dacc acc;
             for (int a = 0; a < n; ++a) {
@@ -199,7 +208,7 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride[other[1]]), T[1][b]);
                 df_mac(acc, df_done(t), T[0][a]);
             }
-            w[k] = df_done(acc);
+            wk = df_done(acc);
         } else {
             dacc acc;
             for (int a = 0; a < n; ++a) {
@@ -212,9 +221,14 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 }
                 df_mac(acc, df_done(ta), T[0][a]);
             }
-            w[k] = df_done(acc);
+            wk = df_done(acc);
         }
+        w_sm[nl][k] = make_float2(wk.hi, wk.lo);
     }
+    __syncwarp();       // a node's eight threads share a warp
+    if (grp != 0 || !valid) return;
+    dfl w[kGameNMax];
+    for (int k = 0; k < n; ++k) w[k] = dfl{w_sm[nl][k].x, w_sm[nl][k].y};
     // Step 3
     double xr[4], pb[4];
     node_coords(g, j, xr, pb);
@@ -285,9 +299,9 @@ cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J
         game_coef_df_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, d_stat);
         CHEB_CUDA_TRY(cudaGetLastError());
     }
-    const unsigned node_blocks = (unsigned)((NP + 127) / 128);
+    const unsigned node_blocks = (unsigned)((NP + kDfNodes - 1) / kDfNodes);
     ProfScope prof("game_player_df", st);
-    game_player_df_kernel<<<dim3(node_blocks, J, B), 128, 0, st>>>(d_inst, d_stat);
+    game_player_df_kernel<<<dim3(node_blocks, J, B), kDfGroup * kDfNodes, 0, st>>>(d_inst, d_stat);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
