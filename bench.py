@@ -120,7 +120,7 @@ class ClockSampler:
 # capture (profiles/modeprod_tc_bf16x6_R262144_n33_m64.md), valid only while
 # the kernel source is the one that was profiled (sha256 prefix below).
 PROFILED_TRAFFIC = {
-    ("modeprod_tc R=262144 n=33 m=64 x=f32", "bf16x6"): ("556570ae69da6822", 41798144),
+    ("modeprod_tc R=262144 n=33 m=64 x=f32", "bf16x6"): ("cd5024a2916dd4c0", 41817088),
 }
 
 
