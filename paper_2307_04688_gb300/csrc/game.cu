@@ -333,6 +333,11 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         g.h = o.h;
         g.delta = 1.0 - p.rho * o.h;
         g.P_M = o.P_M;
+        for (int t = 0; t < J; ++t) {
+            g.slope[t] = 2.0 * o.h * p.beta[t] / o.P_M;
+            g.hA[t] = o.h * p.A[t];
+            g.hphi2[t] = -0.5 * o.h * p.phi[t];
+        }
         g.U_M = o.U_M;
         g.tol = o.tol;
         g.max_iter = o.max_iter;

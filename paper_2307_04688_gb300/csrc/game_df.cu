@@ -233,10 +233,10 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     double xr[4], pb[4];
     node_coords(g, j, xr, pb);
     const double ui = g.u[i * NP + j];
-    const double slope = 2.0 * g.h * g.beta[i] / g.P_M;
+    const double slope = g.slope[i];
     const double xc = g.X[i * NP + j] - slope * ui;
-    const double hA = g.h * g.A[i];
-    const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+    const double hA = g.hA[i];
+    const double hG0 = g.hphi2[i] * pb[i] * pb[i];
     float wf[kGameNMax];
     for (int k = 0; k < n; ++k) wf[k] = w[k].hi + w[k].lo;
     const float U_M = (float)g.U_M;

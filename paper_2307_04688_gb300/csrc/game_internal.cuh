@@ -17,6 +17,9 @@ struct GameDev {
     double K[16], minv;           // neighbour matrix, 1/m
     double A[4], beta[4], phi[4], c[4];
     double h, delta, P_M, U_M, tol;
+    // per player, formed on the host: dx_i/du_i = 2 h beta_i / P_M, h A_i and
+    // -h phi_i / 2 (the FP64 pipe is slow; no division per node)
+    double slope[4], hA[4], hphi2[4];
     long long max_iter;
     int polish, stall_window;
     double *C;                    // J x NP coefficient tensors of the current iterate
@@ -130,10 +133,10 @@ __device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, in
     node_coords(g, j, xr, pb);
     const int NP = g.NP;
     const double ui = g.u[i * NP + j];
-    const double slope = 2.0 * g.h * g.beta[i] / g.P_M;           // dx_i / du_i
+    const double slope = g.slope[i];                               // dx_i / du_i
     const double xc = g.X[i * NP + j] - slope * ui;
-    const double hA = g.h * g.A[i];
-    const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+    const double hA = g.hA[i];
+    const double hG0 = g.hphi2[i] * pb[i] * pb[i];
     double V;
     const double us = argmax_control(w, g.n, xc, slope, hA, hG0, g.h, g.delta, g.U_M, ui, &V);
     g.u_new[i * NP + j] = us;

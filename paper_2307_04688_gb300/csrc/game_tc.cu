@@ -442,13 +442,15 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             float w[NN];
 #pragma unroll
             for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
-            double xr[4], pb[4];
-            node_coords(g, j, xr, pb);
+            // the node's own coordinate (j = j_0 n^2 + j_1 n + j_2) and the
+            // per-player constants formed on the host
+            const int ki = i == 0 ? j / (NN * NN) : i == 1 ? (j / NN) % NN : j % NN;
+            const double pbi = 0.5 * g.P_M * (g.nodes[ki] + 1.0);
             const double ui = g.u[i * NP + j];
-            const double slope = 2.0 * g.h * g.beta[i] / g.P_M;
+            const double slope = g.slope[i];
             const double xc = g.X[i * NP + j] - slope * ui;
-            const double hA = g.h * g.A[i];
-            const double hG0 = -0.5 * g.h * g.phi[i] * pb[i] * pb[i];
+            const double hA = g.hA[i];
+            const double hG0 = g.hphi2[i] * pbi * pbi;
             const float U_M = (float)g.U_M;
             float u = fminf(fmaxf((float)ui, 0.0f), U_M);
             float W, W1, W2;
