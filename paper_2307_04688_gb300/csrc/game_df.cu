@@ -168,7 +168,9 @@ constexpr int kDfNodes = 16;          // nodes per block of 128 threads
 __global__ void __launch_bounds__(kDfGroup * kDfNodes)
 game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats)
 {
-    __shared__ float2 w_sm[kDfNodes][kGameNMax];
+    __shared__ float2 w_sm[kDfNodes][kGameNMax];     // w[k] of each node (double-float)
+    __shared__ float wf_sm[kDfNodes][kGameNMax];     // and rounded to FP32 (the Newton search)
+    __shared__ float2 T_sm[kDfNodes][3][kGameNMax];  // T_k of the next state in each other mode
     const int inst = blockIdx.z, i = blockIdx.y;
     GameStat *st = &stats[inst];
     if (st->done || st->mode != 2) return;
@@ -184,8 +186,17 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     int other[3], no = 0;
     for (int s = 0; s < J; ++s)
         if (s != i) other[no++] = s;
-    dfl T[3][kGameNMax];
-    for (int q = 0; q < no; ++q) df_row(n, g.X[other[q] * NP + jc], T[q]);
+    // the node's T rows, one other mode per thread, shared by its eight threads
+    if (grp < no) {
+        dfl Tr[kGameNMax];
+        df_row(n, g.X[other[grp] * NP + jc], Tr);
+        for (int k = 0; k < n; ++k) T_sm[nl][grp][k] = make_float2(Tr[k].hi, Tr[k].lo);
+    }
+    __syncthreads();
+    auto Tq = [&](int q, int a) {
+        const float2 v = T_sm[nl][q][a];
+        return dfl{v.x, v.y};
+    };
     const float2 *C = reinterpret_cast<const float2 *>(g.Cdf) + (size_t)i * NP;
     auto coef = [&](size_t idx) {
         const float2 v = __ldg(C + idx);
@@ -198,15 +209,15 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             wk = coef(ck);
         } else if (no == 1) {
             dacc acc;
-            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride[other[0]]), T[0][a]);
+            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride[other[0]]), Tq(0, a));
             wk = df_done(acc);
         } else if (no == 2) {
             dacc acc;
             for (int a = 0; a < n; ++a) {
                 dacc t;
                 const size_t ca = ck + (size_t)a * stride[other[0]];
-                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride[other[1]]), T[1][b]);
-                df_mac(acc, df_done(t), T[0][a]);
+                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride[other[1]]), Tq(1, b));
+                df_mac(acc, df_done(t), Tq(0, a));
             }
             wk = df_done(acc);
         } else {
@@ -216,19 +227,20 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 for (int b = 0; b < n; ++b) {
                     dacc t;
                     const size_t cab = ck + (size_t)a * stride[other[0]] + (size_t)b * stride[other[1]];
-                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride[other[2]]), T[2][c]);
-                    df_mac(ta, df_done(t), T[1][b]);
+                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride[other[2]]), Tq(2, c));
+                    df_mac(ta, df_done(t), Tq(1, b));
                 }
-                df_mac(acc, df_done(ta), T[0][a]);
+                df_mac(acc, df_done(ta), Tq(0, a));
             }
             wk = df_done(acc);
         }
         w_sm[nl][k] = make_float2(wk.hi, wk.lo);
+        wf_sm[nl][k] = wk.hi + wk.lo;
     }
     __syncwarp();       // a node's eight threads share a warp
     if (grp != 0 || !valid) return;
-    dfl w[kGameNMax];
-    for (int k = 0; k < n; ++k) w[k] = dfl{w_sm[nl][k].x, w_sm[nl][k].y};
+    const dfl *w = reinterpret_cast<const dfl *>(w_sm[nl]);
+    const float *wf = wf_sm[nl];
     // Step 3
     double xr[4], pb[4];
     node_coords(g, j, xr, pb);
@@ -237,8 +249,6 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const double xc = g.X[i * NP + j] - slope * ui;
     const double hA = g.hA[i];
     const double hG0 = g.hphi2[i] * pb[i] * pb[i];
-    float wf[kGameNMax];
-    for (int k = 0; k < n; ++k) wf[k] = w[k].hi + w[k].lo;
     const float U_M = (float)g.U_M;
     float u = fminf(fmaxf((float)ui, 0.0f), U_M);
     float W, W1, W2;
