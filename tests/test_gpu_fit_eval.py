@@ -200,3 +200,28 @@ def test_fp64_inputs_round_like_cuda(ctx, prec):
     assert torch.equal(a, b)
     P = dev(rng.uniform(-1, 1, (300, 3)))
     assert torch.equal(cb.cheb_eval_points(ctx, cd, P, prec=prec), cb.cheb_eval_points(ctx, cr, P, prec=prec))
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_k_tail_shapes(ctx, prec):
+    """n = 16q + 1 and 16q + 2 (BF16) or 8q + 1 and 8q + 2 (TF32) leave one or two K columns
+    beyond the tensor cores' K, added in FP32 in the epilogue: grid evaluation (T rows formed
+    in the kernel) and point evaluation (the FP64 T matrix passed as B) on such shapes."""
+    rng = np.random.default_rng(23)
+    shape = (17, 18, 34)
+    c = rng.standard_normal(shape) * 0.8 ** np.add.outer(np.add.outer(np.arange(17), np.arange(18)),
+                                                           np.arange(34))
+    d = 3
+    a, b = np.array([-1.0, 0.0, -2.0]), np.array([1.0, 2.0, 1.0])
+    xs = [rng.uniform(a[s], b[s], k) for s, k in enumerate((40, 17, 33))]
+    ref = O.eval_grid(c, xs, a, b)
+    out = cb.cheb_eval_grid(ctx, dev(c), [dev(x) for x in xs], a, b, prec=prec)
+    assert err(out, ref) < 8 * split_bound(prec, d, c, ref)
+    # point evaluation puts the trailing mode on the tensor cores (its leading modes'
+    # product must stay <= 256): trailing n = 34 (tail 2) and 17 (tail 1)
+    for pshape in ((9, 17, 34), (9, 18, 17)):
+        cp = rng.standard_normal(pshape)
+        P = np.stack([rng.uniform(a[s], b[s], 1000) for s in range(d)], axis=1)
+        refp = O.eval_points(cp, P, a, b)
+        outp = cb.cheb_eval_points(ctx, dev(cp), dev(P), a, b, prec=prec)
+        assert err(outp, refp) < 8 * split_bound(prec, d, cp, refp)
