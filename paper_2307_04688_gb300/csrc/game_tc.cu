@@ -14,9 +14,11 @@
 //    shared-memory layout, chunk by chunk (<= 256 columns), and each chunk is
 //    brought in by one bulk copy (TMA engine), double-buffered;
 //  - for n = 16 q + 1 (17, 33) the tensor cores take k_a, k_b < n - 1 with no
-//    padding, and the k_a = n - 1 row and k_b = n - 1 column of C_i become two
-//    FP32 dot products per (node, k_i) in the epilogue, overlapping the next
-//    chunk's MMA (a third of the MMA work at n = 33, half at n = 17);
+//    padding (a third of the MMA work at n = 33, half at n = 17); the
+//    k_b = n - 1 column of C_i rides along as 16 extra B columns per chunk
+//    (one per k_i of the chunk), and the k_a = n - 1 row is one FP32 dot
+//    product per (node, k_i) in the epilogue, its coefficients read from
+//    shared memory by 16-byte broadcast loads;
 //  - tcgen05.mma accumulates the split products of a chunk in TMEM (FP32);
 //  - the epilogue reads TMEM, multiplies by T_{k_b}(x_b(j)) (kept in
 //    registers) and writes w_j[k_i] to shared memory;
@@ -63,8 +65,10 @@ template <> struct GForm<CHEB_TF32X3> {
 template <int FORM, int NN, int CH> struct Shape {
     using F = GForm<FORM>;
     // n = 16 q + 1 (the Lobatto sizes 17, 33): the tensor cores take k_a, k_b
-    // < n - 1 with no padding; the k_a = n - 1 row and the k_b = n - 1 column
-    // of C_i are two FP32 dot products per (node, k_i) in the epilogue
+    // < n - 1 with no padding, plus the k_b = n - 1 column of C_i as a group
+    // of TCOL extra B columns at the front of each chunk (column k_l holds
+    // C[k_i, k_a, n-1]); the k_a = n - 1 row is one FP32 dot product per
+    // (node, k_i) in the epilogue
     static constexpr int TAIL = (NN > 16 && (NN - 1) % 16 == 0) ? 1 : 0;
     static constexpr int NM = NN - TAIL;                              // k_a, k_b on the tensor cores
     static constexpr int NBP = (NM + 15) / 16 * 16;                 // k_b padded
@@ -72,23 +76,27 @@ template <int FORM, int NN, int CH> struct Shape {
     static constexpr int E = 16 / F::EB;                            // K elements per 16 bytes
     static constexpr int KC = KP / E;                               // 16-byte chunks along K
     static constexpr int CHKI = CH;                                 // k_i per column chunk
-    static_assert(CH >= 1 && CH <= NN && CH * NBP <= 256, "column chunk out of range");
+    static constexpr int TCOL = TAIL ? 16 : 0;                      // tail columns per chunk
+    static_assert(CH >= 1 && CH <= NN && CH * NBP + TCOL <= 256 && CH <= 16, "column chunk out of range");
     static constexpr int NCH = (NN + CHKI - 1) / CHKI;              // column chunks
-    static constexpr int NC = CHKI * NBP;                           // columns of a stored chunk
+    static constexpr int NC = TCOL + CHKI * NBP;                    // columns of a stored chunk
     static constexpr int SPLIT_BYTES = NC * KP * F::EB;             // one split part of a chunk
     static constexpr int CHUNK_BYTES = F::SB * SPLIT_BYTES;
     static constexpr int A_SPLIT = kTile * KP * F::EB;
     static constexpr int TMEM_COLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;   // one buffer
     static constexpr int TMEM_ALLOC = 2 * TMEM_COLS;                // two accumulators (<= 512)
-    // FP32 tail coefficients per player: Ca[k_i][k_b] = C[k_i, n-1, k_b] (k_b < n),
-    // Cb[k_i][k_a] = C[k_i, k_a, n-1] (k_a < n - 1)
-    static constexpr int TAIL_FLOATS = TAIL ? 2 * NN * NN : 0;
+    // FP32 tail coefficients per player, Ca[k_i][k_b] = C[k_i, n-1, k_b]
+    // (k_b < n), rows padded to CAP floats for 16-byte loads
+    static constexpr int CAP = (NN + 3) / 4 * 4;
+    static constexpr int TAIL_FLOATS = TAIL ? NN * CAP : 0;
     static constexpr size_t PLAYER_BYTES =     // a multiple of 128: every chunk starts 16-byte aligned
         ((size_t)NCH * CHUNK_BYTES + (size_t)TAIL_FLOATS * sizeof(float) + 127) / 128 * 128;
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) +              // w
-                                   (size_t)TAIL * NN * kTile * sizeof(float) +       // T_{k_a} per row
                                    (size_t)TAIL_FLOATS * sizeof(float) + 128;
+    // CTAs per SM that shared memory allows, at most 2: the register budget
+    // the kernel is compiled to (128 per thread at 2)
+    static constexpr int MINB = 2 * (SMEM + 1024) <= 228 * 1024 ? 2 : 1;
 };
 
 // Column chunks the tuner tries for each node count; the first is the default
@@ -96,8 +104,8 @@ template <int FORM, int NN, int CH> struct Shape {
 template <int NN> struct Chunks;
 template <> struct Chunks<5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };
 template <> struct Chunks<9> { static constexpr int count = 2, v0 = 9, v1 = 3, v2 = 3; };
-template <> struct Chunks<17> { static constexpr int count = 3, v0 = 9, v1 = 6, v2 = 3; };    // N = 144, 96, 48
-template <> struct Chunks<33> { static constexpr int count = 3, v0 = 7, v1 = 5, v2 = 3; };    // N = 224, 160, 96
+template <> struct Chunks<17> { static constexpr int count = 3, v0 = 9, v1 = 6, v2 = 3; };    // N = 160, 112, 64
+template <> struct Chunks<33> { static constexpr int count = 3, v0 = 7, v1 = 5, v2 = 3; };    // N = 240, 176, 112
 
 // ---- helpers -------------------------------------------------------------------
 // T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
@@ -181,8 +189,6 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
         if (stats[q].done || stats[q].mode != 1) continue;
         const GameDev &g = insts[q];
         const int row = e / S::KC, kc = e - row * S::KC;
-        const int kl = row / S::NBP, kb = row - kl * S::NBP;
-        const int ki = c * S::CHKI + kl;
         int a, b;
         other_modes(i, a, b);
         const int si = i == 0 ? NN * NN : i == 1 ? NN : 1;
@@ -190,12 +196,24 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
         const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
         const double *C = g.C + (size_t)i * g.NP;
         float v[S::E];
+        if (row < S::TCOL) {
+            // tail column k_l: C[k_i, k_a, n-1]
+            const int ki = c * S::CHKI + row;
 #pragma unroll
-        for (int k = 0; k < S::E; ++k) {
-            const int ka = kc * S::E + k;
-            v[k] = (ki < NN && kb < S::NM && ka < S::NM)
-                       ? (float)C[ki * si + ka * sa + kb * sb]
-                       : 0.0f;
+            for (int k = 0; k < S::E; ++k) {
+                const int ka = kc * S::E + k;
+                v[k] = (row < S::CHKI && ki < NN && ka < S::NM) ? (float)C[ki * si + ka * sa + (NN - 1) * sb]
+                                                                : 0.0f;
+            }
+        } else {
+            const int mrow = row - S::TCOL;
+            const int kl = mrow / S::NBP, kb = mrow - kl * S::NBP;
+            const int ki = c * S::CHKI + kl;
+#pragma unroll
+            for (int k = 0; k < S::E; ++k) {
+                const int ka = kc * S::E + k;
+                v[k] = (ki < NN && kb < S::NM && ka < S::NM) ? (float)C[ki * si + ka * sa + kb * sb] : 0.0f;
+            }
         }
         uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES + (size_t)c * S::CHUNK_BYTES +
                        (size_t)kc * (S::NC * 16) + (size_t)row * 16;
@@ -217,12 +235,8 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
             const int sa = a == 0 ? NN * NN : a == 1 ? NN : 1;
             const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
             const double *C = g.C + (size_t)i * g.NP;
-            const int half = e / (NN * NN), r = e - half * NN * NN, ki = r / NN, k = r - ki * NN;
-            float v;
-            if (half == 0)
-                v = (float)C[ki * si + (NN - 1) * sa + k * sb];                          // Ca[ki][kb = k]
-            else
-                v = k < NN - 1 ? (float)C[ki * si + k * sa + (NN - 1) * sb] : 0.0f;    // Cb[ki][ka = k]
+            const int ki = e / S::CAP, k = e - ki * S::CAP;
+            const float v = k < NN ? (float)C[ki * si + (NN - 1) * sa + k * sb] : 0.0f;   // Ca[ki][kb = k]
             float *dst = reinterpret_cast<float *>(static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES +
                                                    (size_t)S::NCH * S::CHUNK_BYTES);
             dst[e] = v;
@@ -256,7 +270,7 @@ __device__ __forceinline__ void objective_f32(const float (&w)[NN], float xc, fl
 }
 
 template <int FORM, int NN, int CH>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, (Shape<FORM, NN, CH>::MINB))
 game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B, int *err)
 {
     using S = Shape<FORM, NN, CH>;
@@ -265,8 +279,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     uint8_t *sA = smem;                                         // SA x [128 x KP]
     uint8_t *sB = sA + F::SA * S::A_SPLIT;                      // 2 stages x CHUNK_BYTES
     float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
-    float *ta_s = w_s + NN * kTile;                                   // [NN][128] T_{k_a} of each row (TAIL)
-    float *ct_s = ta_s + S::TAIL * NN * kTile;                        // tail coefficients Ca, Cb (TAIL)
+    float *ct_s = w_s + NN * kTile;                                   // tail coefficients Ca (TAIL)
     uint64_t *bars = reinterpret_cast<uint64_t *>(ct_s + S::TAIL_FLOATS);   // [0,1] B loads, [2,3] mma per accumulator
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
@@ -311,7 +324,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
         if constexpr (S::TAIL) {
             const float *tsrc = reinterpret_cast<const float *>(bsrc + (size_t)S::NCH * S::CHUNK_BYTES);
-            for (int e = tid; e < S::TAIL_FLOATS; e += kThreads) ct_s[e] = tsrc[e];
+            for (int e = tid; e < S::TAIL_FLOATS / 4; e += kThreads)
+                reinterpret_cast<float4 *>(ct_s)[e] = reinterpret_cast<const float4 *>(tsrc)[e];
         }
         if (tid == 0) {
             for (int c = 0; c < 2 && c < S::NCH; ++c) {
@@ -324,7 +338,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const int j = t * kTile + row;
         const bool valid = j < NP;
         float Tb[S::NBP];
-        float tb_last = 0.0f;    // T_{n-1}(x_b) (TAIL)
+        float ta_last = 0.0f, tb_last = 0.0f;    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
         {
             float Ta[NN], Tbn[NN];
             const double xa = valid ? g.X[a * NP + j] : 0.0;
@@ -334,11 +348,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 #pragma unroll
             for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < S::NM) ? Tbn[k] : 0.0f;
             if constexpr (S::TAIL) {
+                ta_last = valid ? Ta[NN - 1] : 0.0f;
                 tb_last = valid ? Tbn[NN - 1] : 0.0f;
-                if (half == 0) {
-#pragma unroll
-                    for (int k = 0; k < NN; ++k) ta_s[k * kTile + row] = valid ? Ta[k] : 0.0f;
-                }
             }
 #pragma unroll
             for (int kc = 0; kc < S::KC; ++kc) {
@@ -361,7 +372,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         auto issue_mma = [&](int c) {
             const int stage = c & 1;
             const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
-            const int N = kis * S::NBP;
+            const int N = S::TCOL + kis * S::NBP;
             if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
             ld_phase ^= 1u << stage;
             pending &= ~(1u << stage);
@@ -408,7 +419,10 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 for (int kl = ehalf; kl < kis; kl += 2) {
                     uint32_t v[S::NBP / 16][16];
 #pragma unroll
-                    for (int g16 = 0; g16 < S::NBP / 16; ++g16) tmem_ld16(lane_addr + kl * S::NBP + g16 * 16, v[g16]);
+                    for (int g16 = 0; g16 < S::NBP / 16; ++g16)
+                        tmem_ld16(lane_addr + S::TCOL + kl * S::NBP + g16 * 16, v[g16]);
+                    uint32_t vt = 0;
+                    if constexpr (S::TAIL) tmem_ld1(lane_addr + kl, vt);
                     tmem_ld_wait();
                     float acc = 0.0f;
 #pragma unroll
@@ -416,18 +430,19 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 #pragma unroll
                         for (int e = 0; e < 16; ++e) acc = fmaf(__uint_as_float(v[g16][e]), Tb[g16 * 16 + e], acc);
                     if constexpr (S::TAIL) {
-                        // T_{n-1}(x_a) sum_{k_b} C[k_i, n-1, k_b] T_{k_b}(x_b)
-                        //   + T_{n-1}(x_b) sum_{k_a < n-1} C[k_i, k_a, n-1] T_{k_a}(x_a)
-                        const int ki = c * S::CHKI + kl;
-                        const float *ca = ct_s + ki * NN;
-                        const float *cb = ct_s + NN * NN + ki * NN;
-                        float ta_dot = ca[NN - 1] * tb_last, tb_dot = 0.0f;
+                        // + T_{n-1}(x_b) sum_{k_a < n-1} C[k_i, k_a, n-1] T_{k_a}(x_a)   (tail column)
+                        //   + T_{n-1}(x_a) sum_{k_b} C[k_i, n-1, k_b] T_{k_b}(x_b)      (FP32)
+                        const float4 *ca = reinterpret_cast<const float4 *>(ct_s + (c * S::CHKI + kl) * S::CAP);
+                        float ta_dot = ct_s[(c * S::CHKI + kl) * S::CAP + NN - 1] * tb_last;
 #pragma unroll
-                        for (int k = 0; k < S::NM; ++k) {
-                            ta_dot = fmaf(ca[k], Tb[k], ta_dot);
-                            tb_dot = fmaf(cb[k], ta_s[k * kTile + r], tb_dot);
+                        for (int k4 = 0; k4 < S::NM / 4; ++k4) {
+                            const float4 cv = ca[k4];
+                            ta_dot = fmaf(cv.x, Tb[4 * k4], ta_dot);
+                            ta_dot = fmaf(cv.y, Tb[4 * k4 + 1], ta_dot);
+                            ta_dot = fmaf(cv.z, Tb[4 * k4 + 2], ta_dot);
+                            ta_dot = fmaf(cv.w, Tb[4 * k4 + 3], ta_dot);
                         }
-                        acc = fmaf(ta_s[(NN - 1) * kTile + r], ta_dot, fmaf(tb_last, tb_dot, acc));
+                        acc = fmaf(ta_last, ta_dot, fmaf(tb_last, __uint_as_float(vt), acc));
                     }
                     w_s[(c * S::CHKI + kl) * kTile + r] = acc;
                 }
@@ -611,7 +626,8 @@ std::string describe(int cfg)
     using C = Chunks<NN>;
     const int c = cfg / 4, chunk = c == 0 ? C::v0 : c == 1 ? C::v1 : C::v2;
     constexpr int nbp = Shape<FORM, NN, C::v0>::NBP;
-    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(chunk * nbp) +
+    constexpr int tcol = Shape<FORM, NN, C::v0>::TCOL;
+    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(tcol + chunk * nbp) +
            ") ctas/SM=" + std::to_string(cfg % 4);
 }
 
