@@ -41,6 +41,7 @@ using namespace tc;
 
 constexpr int kTile = 128;
 constexpr int kThreads = 256;
+constexpr int kProducer = kTile;    // issues the bulk copies and the MMAs (first thread of the upper half)
 
 template <int FORM> struct GForm;
 template <> struct GForm<CHEB_BF16X3> {
@@ -91,9 +92,13 @@ template <int FORM, int NN, int CH> struct Shape {
     static constexpr int TAIL_FLOATS = TAIL ? NN * CAP : 0;
     static constexpr size_t PLAYER_BYTES =     // a multiple of 128: every chunk starts 16-byte aligned
         ((size_t)NCH * CHUNK_BYTES + (size_t)TAIL_FLOATS * sizeof(float) + 127) / 128 * 128;
+    // rows staged by the prologue for the epilogue: T_{k_b} (k_b < NM), and
+    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
+    static constexpr int STG = NM + 2 * TAIL;
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) +              // w
-                                   (size_t)TAIL_FLOATS * sizeof(float) + 128;
+                                   (size_t)TAIL_FLOATS * sizeof(float) +
+                                   (size_t)STG * kTile * sizeof(float) + 128;
     // CTAs per SM that shared memory allows, at most 2: the register budget
     // the kernel is compiled to (128 per thread at 2)
     static constexpr int MINB = 2 * (SMEM + 1024) <= 228 * 1024 ? 2 : 1;
@@ -280,7 +285,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     uint8_t *sB = sA + F::SA * S::A_SPLIT;                      // 2 stages x CHUNK_BYTES
     float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
     float *ct_s = w_s + NN * kTile;                                   // tail coefficients Ca (TAIL)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ct_s + S::TAIL_FLOATS);   // [0,1] B loads, [2,3] mma per accumulator
+    float *tb_s = ct_s + S::TAIL_FLOATS;                              // [STG][128] staged T_{k_b}, T_{n-1}
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tb_s + S::STG * kTile);   // [0,1] B loads, [2,3] mma per accumulator
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -305,107 +311,140 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const int NP = NN * NN * NN;
     const int tiles = (NP + kTile - 1) / kTile;
     const int64_t items = (int64_t)B * 3 * tiles;
-    uint32_t ld_phase = 0, mma_phase = 0;   // bit s: parity of B stage s / of accumulator s
-    uint32_t pending = 0;                   // bit s: a copy into stage s is in flight
+    // producer-thread state (tid == kProducer)
+    uint32_t ld_phase = 0;     // bit s: parity of B stage s
+    uint32_t pending = 0;      // bit s: a copy into stage s is in flight
+    uint32_t mma_out = 0;      // bit s: an MMA commit on accumulator s not yet waited for
+    uint32_t mma_phase = 0;    // bit s: parity of accumulator s (every thread)
 
     const int row = tid & (kTile - 1);
     const int half = tid >> 7;
     const int quarter = warp & 3, ehalf = warp >> 2;
 
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int t = (int)(item % tiles);
-        const int i = (int)((item / tiles) % 3);
-        const int q = (int)(item / (tiles * 3));
-        GameStat *st = &stats[q];
-        if (st->done || st->mode != 1) continue;     // uniform across the block
+    // the next work item at or after `from` whose instance is still iterating
+    // in split precision (uniform across the block)
+    auto next_item = [&](int64_t from) {
+        for (int64_t it = from; it < items; it += gridDim.x) {
+            const int q = (int)(it / (tiles * 3));
+            if (!stats[q].done && stats[q].mode == 1) return it;
+        }
+        return items;
+    };
+    // MMA of chunk c into accumulator c & 1 (producer thread); the accumulator
+    // of chunk c + 1 is filled while the epilogue drains chunk c
+    auto issue_mma = [&](int c) {
+        const int stage = c & 1;
+        const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
+        const int N = S::TCOL + kis * S::NBP;
+        if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
+        ld_phase ^= 1u << stage;
+        pending &= ~(1u << stage);
+        tc_fence_after();
+        const uint32_t idesc = make_idesc(F::FMT, kTile, N);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(stage * S::TMEM_COLS);
+#pragma unroll
+        for (int p = 0; p < F::NPROD; ++p) {
+            const uint32_t ab = a0 + F::pa(p) * S::A_SPLIT;
+            const uint32_t bb = b0 + F::pb(p) * S::SPLIT_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < S::KC / 2; ++ks) {
+                const uint64_t ad = make_sdesc(ab + ks * 2 * (kTile * 16), kTile * 16, 128);
+                const uint64_t bd = make_sdesc(bb + ks * 2 * (S::NC * 16), S::NC * 16, 128);
+                if constexpr (F::FMT == 2)
+                    mma_tf32(acc, ad, bd, idesc, (p | ks) != 0);
+                else
+                    mma_bf16(acc, ad, bd, idesc, (p | ks) != 0);
+            }
+        }
+        mma_commit(&bars[2 + stage]);
+        mma_out |= 1u << stage;
+    };
+    // Prologue of a tile, run by the upper 128 threads (one per node of the
+    // tile) while the lower 128 finish the previous tile's Step 3: the tail
+    // coefficients and the first two B chunks are brought in, the A operand
+    // T_{k_a}(x_a(j)) is formed and split, T_{k_b}(x_b(j)) is staged for the
+    // epilogue, and chunk 0's MMA is issued.
+    auto prologue = [&](int64_t it) {
+        const int t = (int)(it % tiles);
+        const int i = (int)((it / tiles) % 3);
+        const int q = (int)(it / (tiles * 3));
         const GameDev &g = insts[q];
         int a, b;
         other_modes(i, a, b);
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
-        if constexpr (S::TAIL) {
-            const float *tsrc = reinterpret_cast<const float *>(bsrc + (size_t)S::NCH * S::CHUNK_BYTES);
-            for (int e = tid; e < S::TAIL_FLOATS / 4; e += kThreads)
-                reinterpret_cast<float4 *>(ct_s)[e] = reinterpret_cast<const float4 *>(tsrc)[e];
-        }
-        if (tid == 0) {
+        if (tid == kProducer)
             for (int c = 0; c < 2 && c < S::NCH; ++c) {
                 mbar_arrive_expect_tx(&bars[c], S::CHUNK_BYTES);
                 bulk_g2s(sB + c * S::CHUNK_BYTES, bsrc + (size_t)c * S::CHUNK_BYTES, S::CHUNK_BYTES, &bars[c]);
                 pending |= 1u << c;
             }
+        if constexpr (S::TAIL) {
+            const float *tsrc = reinterpret_cast<const float *>(bsrc + (size_t)S::NCH * S::CHUNK_BYTES);
+            for (int e = row; e < S::TAIL_FLOATS / 4; e += kTile)
+                reinterpret_cast<float4 *>(ct_s)[e] = reinterpret_cast<const float4 *>(tsrc)[e];
         }
-        // A operand and the epilogue factor for this thread's row (node)
         const int j = t * kTile + row;
         const bool valid = j < NP;
-        float Tb[S::NBP];
-        float ta_last = 0.0f, tb_last = 0.0f;    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
-        {
-            float Ta[NN], Tbn[NN];
-            const double xa = valid ? g.X[a * NP + j] : 0.0;
-            const double xb = valid ? g.X[b * NP + j] : 0.0;
-            cheb_row_f32<NN>(xa, Ta);
-            cheb_row_f32<NN>(xb, Tbn);
+        float Ta[NN], Tbn[NN];
+        const double xa = valid ? g.X[a * NP + j] : 0.0;
+        const double xb = valid ? g.X[b * NP + j] : 0.0;
+        cheb_row_f32<NN>(xa, Ta);
+        cheb_row_f32<NN>(xb, Tbn);
 #pragma unroll
-            for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < S::NM) ? Tbn[k] : 0.0f;
-            if constexpr (S::TAIL) {
-                ta_last = valid ? Ta[NN - 1] : 0.0f;
-                tb_last = valid ? Tbn[NN - 1] : 0.0f;
+        for (int k = 0; k < S::NM; ++k) tb_s[k * kTile + row] = valid ? Tbn[k] : 0.0f;
+        if constexpr (S::TAIL) {
+            tb_s[S::NM * kTile + row] = valid ? Ta[NN - 1] : 0.0f;
+            tb_s[(S::NM + 1) * kTile + row] = valid ? Tbn[NN - 1] : 0.0f;
+        }
+#pragma unroll
+        for (int kc = 0; kc < S::KC; ++kc) {
+            float v[S::E];
+#pragma unroll
+            for (int e = 0; e < S::E; ++e) {
+                const int k = kc * S::E + e;
+                v[e] = (valid && k < S::NM) ? Ta[k < S::NM ? k : 0] : 0.0f;
             }
-#pragma unroll
-            for (int kc = 0; kc < S::KC; ++kc) {
-                if ((kc & 1) != half) continue;
-                float v[S::E];
-#pragma unroll
-                for (int e = 0; e < S::E; ++e) {
-                    const int k = kc * S::E + e;
-                    v[e] = (valid && k < S::NM) ? Ta[k < S::NM ? k : 0] : 0.0f;
-                }
-                split_store16<FORM, F::SA>(v, sA + (uint32_t)kc * (kTile * 16) + row * 16, S::A_SPLIT);
-            }
+            split_store16<FORM, F::SA>(v, sA + (uint32_t)kc * (kTile * 16) + row * 16, S::A_SPLIT);
         }
         fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // MMA of chunk c into accumulator c & 1 (thread 0); the accumulator of
-        // chunk c + 1 is filled while the epilogue drains chunk c
-        auto issue_mma = [&](int c) {
-            const int stage = c & 1;
-            const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
-            const int N = S::TCOL + kis * S::NBP;
-            if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
-            ld_phase ^= 1u << stage;
-            pending &= ~(1u << stage);
-            tc_fence_after();
-            const uint32_t idesc = make_idesc(F::FMT, kTile, N);
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
-            const uint32_t acc = tmem + (uint32_t)(stage * S::TMEM_COLS);
+        named_barrier_sync(1, kTile);
+        if (tid == kProducer) issue_mma(0);
+    };
+
+    int64_t item = next_item(blockIdx.x);
+    if (item < items && half == 1) prologue(item);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    while (item < items) {
+        const int t = (int)(item % tiles);
+        const int i = (int)((item / tiles) % 3);
+        const int q = (int)(item / (tiles * 3));
+        GameStat *st = &stats[q];
+        const GameDev &g = insts[q];
+        const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
+        const int j = t * kTile + row;
+        const bool valid = j < NP;
+        // the epilogue factor T_{k_b}(x_b(j)) of this thread's row, from the stage
+        float Tb[S::NBP];
 #pragma unroll
-            for (int p = 0; p < F::NPROD; ++p) {
-                const uint32_t ab = a0 + F::pa(p) * S::A_SPLIT;
-                const uint32_t bb = b0 + F::pb(p) * S::SPLIT_BYTES;
-#pragma unroll
-                for (int ks = 0; ks < S::KC / 2; ++ks) {
-                    const uint64_t ad = make_sdesc(ab + ks * 2 * (kTile * 16), kTile * 16, 128);
-                    const uint64_t bd = make_sdesc(bb + ks * 2 * (S::NC * 16), S::NC * 16, 128);
-                    if constexpr (F::FMT == 2)
-                        mma_tf32(acc, ad, bd, idesc, (p | ks) != 0);
-                    else
-                        mma_bf16(acc, ad, bd, idesc, (p | ks) != 0);
-                }
-            }
-            mma_commit(&bars[2 + stage]);
-        };
-        if (tid == 0) issue_mma(0);
+        for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < S::NM) ? tb_s[k * kTile + row] : 0.0f;
+        float ta_last = 0.0f, tb_last = 0.0f;    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
+        if constexpr (S::TAIL) {
+            ta_last = tb_s[S::NM * kTile + row];
+            tb_last = tb_s[(S::NM + 1) * kTile + row];
+        }
         for (int c = 0; c < S::NCH; ++c) {
             const int buf = c & 1;
             const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
-            if (tid == 0 && c + 1 < S::NCH) issue_mma(c + 1);
+            if (tid == kProducer && c + 1 < S::NCH) issue_mma(c + 1);
             if (!mbar_wait_bounded(&bars[2 + buf], (mma_phase >> buf) & 1u, err)) *abort_flag = 1;
             mma_phase ^= 1u << buf;
+            mma_out &= ~(1u << buf);
             tc_fence_after();
             // the B stage of chunk c is free again: prefetch chunk c + 2 into it
-            if (tid == 0 && c + 2 < S::NCH) {
+            if (tid == kProducer && c + 2 < S::NCH) {
                 mbar_arrive_expect_tx(&bars[buf], S::CHUNK_BYTES);
                 bulk_g2s(sB + buf * S::CHUNK_BYTES, bsrc + (size_t)(c + 2) * S::CHUNK_BYTES, S::CHUNK_BYTES,
                          &bars[buf]);
@@ -452,89 +491,100 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             if (*abort_flag) break;
         }
         if (*abort_flag) break;
-        // Step 3 for each node of the tile: one thread per node
-        if (tid < kTile && valid) {
-            float w[NN];
+        const int64_t next = next_item(item + gridDim.x);
+        if (half == 0) {
+            // Step 3 for each node of the tile: one thread per node
+            if (valid) {
+                float w[NN];
 #pragma unroll
-            for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
-            // the node's own coordinate (j = j_0 n^2 + j_1 n + j_2) and the
-            // per-player constants formed on the host
-            const int ki = i == 0 ? j / (NN * NN) : i == 1 ? (j / NN) % NN : j % NN;
-            const double pbi = 0.5 * g.P_M * (g.nodes[ki] + 1.0);
-            const double ui = g.u[i * NP + j];
-            const double slope = g.slope[i];
-            const double xc = g.X[i * NP + j] - slope * ui;
-            const double hA = g.hA[i];
-            const double hG0 = g.hphi2[i] * pbi * pbi;
-            const float U_M = (float)g.U_M;
-            float u = fminf(fmaxf((float)ui, 0.0f), U_M);
-            float W, W1, W2;
-            for (int itn = 0; itn < 12; ++itn) {
-                objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
-                float un = (W2 < 0.0f) ? u - W1 / W2 : (W1 > 0.0f ? 0.5f * (u + U_M) : 0.5f * u);
-                un = fminf(fmaxf(un, 0.0f), U_M);
-                const float step = fabsf(un - u);
-                u = un;
-                if (step <= 1e-7f * U_M) break;
-            }
-            // W at a control: the series sum_m w_m T_m(x) in double-float
-            // (T by the recurrence in double-float, products and sums
-            // error-free), the rest in FP64
-            auto value64 = [&](double uu) {
-                const double x = xc + slope * uu;
-                const ff xf = ff_from_double(x);
-                const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
-                ff t0 = {1.0f, 0.0f}, t1 = xf;
-                double s = (double)w[0] + (double)w[1] * ((double)xf.hi + (double)xf.lo);
-                ff acc = {0.0f, 0.0f};
-#pragma unroll
-                for (int m = 2; m < NN; ++m) {
-                    const ff t2 = ff_cheb_step(x2, t1, t0);
-                    // acc += w_m * t2 (error-free product, compensated sum)
-                    const float p = w[m] * t2.hi;
-                    float e = fmaf(w[m], t2.hi, -p);
-                    e = fmaf(w[m], t2.lo, e);
-                    const float sh = acc.hi + p;
-                    const float bb = sh - acc.hi;
-                    const float er = (acc.hi - (sh - bb)) + (p - bb);
-                    float lo = acc.lo + e + er;
-                    acc.hi = sh + lo;
-                    acc.lo = lo - (acc.hi - sh);
-                    t0 = t1;
-                    t1 = t2;
+                for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
+                // the node's own coordinate (j = j_0 n^2 + j_1 n + j_2) and the
+                // per-player constants formed on the host
+                const int ki = i == 0 ? j / (NN * NN) : i == 1 ? (j / NN) % NN : j % NN;
+                const double pbi = 0.5 * g.P_M * (g.nodes[ki] + 1.0);
+                const double ui = g.u[i * NP + j];
+                const double slope = g.slope[i];
+                const double xc = g.X[i * NP + j] - slope * ui;
+                const double hA = g.hA[i];
+                const double hG0 = g.hphi2[i] * pbi * pbi;
+                const float U_M = (float)g.U_M;
+                float u = fminf(fmaxf((float)ui, 0.0f), U_M);
+                float W, W1, W2;
+                for (int itn = 0; itn < 12; ++itn) {
+                    objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+                    float un = (W2 < 0.0f) ? u - W1 / W2 : (W1 > 0.0f ? 0.5f * (u + U_M) : 0.5f * u);
+                    un = fminf(fmaxf(un, 0.0f), U_M);
+                    const float step = fabsf(un - u);
+                    u = un;
+                    if (step <= 1e-7f * U_M) break;
                 }
-                s += (double)acc.hi + (double)acc.lo;
-                return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
-            };
-            objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
-            double us = (double)u;
-            double V;
-            if (u > 0.0f && u < U_M && W2 < 0.0f) {
-                // a concave stationary point inside (0, U_M): the maximiser
-                V = value64(us);
-            } else {
-                // at a bound or not concave: the bounds and the Newton point
-                // compete in FP64 (differences of W near a bound are far below
-                // FP32 resolution), ties to the smaller control
-                double bu = 0.0, bv = value64(0.0);
-                const double vn = value64(us);
-                if (vn > bv) { bv = vn; bu = us; }
-                const double vm = value64(g.U_M);
-                if (vm > bv) { bv = vm; bu = g.U_M; }
-                us = bu;
-                V = bv;
+                // W at a control: the series sum_m w_m T_m(x) in double-float
+                // (T by the recurrence in double-float, products and sums
+                // error-free), the rest in FP64
+                auto value64 = [&](double uu) {
+                    const double x = xc + slope * uu;
+                    const ff xf = ff_from_double(x);
+                    const ff x2 = {2.0f * xf.hi, 2.0f * xf.lo};
+                    ff t0 = {1.0f, 0.0f}, t1 = xf;
+                    double s = (double)w[0] + (double)w[1] * ((double)xf.hi + (double)xf.lo);
+                    ff acc = {0.0f, 0.0f};
+#pragma unroll
+                    for (int m = 2; m < NN; ++m) {
+                        const ff t2 = ff_cheb_step(x2, t1, t0);
+                        // acc += w_m * t2 (error-free product, compensated sum)
+                        const float p = w[m] * t2.hi;
+                        float e = fmaf(w[m], t2.hi, -p);
+                        e = fmaf(w[m], t2.lo, e);
+                        const float sh = acc.hi + p;
+                        const float bb = sh - acc.hi;
+                        const float er = (acc.hi - (sh - bb)) + (p - bb);
+                        float lo = acc.lo + e + er;
+                        acc.hi = sh + lo;
+                        acc.lo = lo - (acc.hi - sh);
+                        t0 = t1;
+                        t1 = t2;
+                    }
+                    s += (double)acc.hi + (double)acc.lo;
+                    return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
+                };
+                objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
+                double us = (double)u;
+                double V;
+                if (u > 0.0f && u < U_M && W2 < 0.0f) {
+                    // a concave stationary point inside (0, U_M): the maximiser
+                    V = value64(us);
+                } else {
+                    // at a bound or not concave: the bounds and the Newton point
+                    // compete in FP64 (differences of W near a bound are far below
+                    // FP32 resolution), ties to the smaller control
+                    double bu = 0.0, bv = value64(0.0);
+                    const double vn = value64(us);
+                    if (vn > bv) { bv = vn; bu = us; }
+                    const double vm = value64(g.U_M);
+                    if (vm > bv) { bv = vm; bu = g.U_M; }
+                    us = bu;
+                    V = bv;
+                }
+                g.u_new[i * NP + j] = us;
+                g.Vn_new[i * NP + j] = V;
+                const double d = fabs(V - g.Vn[i * NP + j]);
+                atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
             }
-            g.u_new[i * NP + j] = us;
-            g.Vn_new[i * NP + j] = V;
-            const double d = fabs(V - g.Vn[i * NP + j]);
-            atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
+        } else if (next < items) {
+            prologue(next);
         }
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
+        item = next;
     }
-    // drain copies in flight (abort path), free TMEM
-    if (tid == 0)
+    // drain copies and MMAs in flight (abort path), free TMEM
+    if (tid == kProducer) {
         for (int s2 = 0; s2 < 2; ++s2)
             if (pending & (1u << s2)) mbar_wait_bounded(&bars[s2], (ld_phase >> s2) & 1u, err);
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (mma_out & (1u << s2)) mbar_wait_bounded(&bars[2 + s2], (mma_phase >> s2) & 1u, err);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

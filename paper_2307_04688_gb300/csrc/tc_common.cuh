@@ -144,6 +144,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+// Barrier `id` (1..15) over the first `count` threads that reach it (a
+// multiple of 32; every warp of the group must arrive).
+__device__ __forceinline__ void named_barrier_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // One 32-bit column: thread i of the warp receives lane (32 * (warp % 4) + i).
 __device__ __forceinline__ void tmem_ld1(uint32_t taddr, uint32_t &r)
 {
