@@ -509,6 +509,9 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 const double hG0 = g.hphi2[i] * pbi * pbi;
                 const float U_M = (float)g.U_M;
                 float u = fminf(fmaxf((float)ui, 0.0f), U_M);
+                // Newton on W'(u) = 0; W'' of the last iterate decides below
+                // whether the stationary point is a concave interior maximiser
+                // (the final step is below 1e-7 U_M)
                 float W, W1, W2;
                 for (int itn = 0; itn < 12; ++itn) {
                     objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
@@ -547,7 +550,6 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                     s += (double)acc.hi + (double)acc.lo;
                     return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
                 };
-                objective_f32<NN>(w, (float)xc, (float)slope, (float)hA, (float)g.h, (float)g.delta, u, W, W1, W2);
                 double us = (double)u;
                 double V;
                 if (u > 0.0f && u < U_M && W2 < 0.0f) {
