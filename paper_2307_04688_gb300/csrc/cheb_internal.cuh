@@ -83,6 +83,22 @@ namespace cheb {
 cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t R, int n, int m,
                          cudaStream_t st);
 
+// Slabs to leave alone in modeprod_f64_slabs: slab g is skipped when
+// flags[(g / per_flag) * stride] != 0 (no flags: none is).
+struct SlabSkip {
+    const int *flags = nullptr;
+    int64_t stride = 0;      // in ints
+    int64_t per_flag = 1;    // slabs per flag
+};
+
+// The same product on G slabs of R rows each, every slab moving its new mode
+// to its own front: out[(g m + j) R + r] = sum_k B[j * n + k] X[(g R + r) n + k].
+// Applied d times it takes each slab's tensor through all its modes and back
+// to their original order, slab by slab. Rows of skipped slabs are neither
+// computed nor written.
+cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, int64_t G, int64_t R, int n, int m,
+                               const SlabSkip &skip, cudaStream_t st);
+
 // T[j * n + l] = T_l(x~_j), x~_j = (2 x[j * stride] - a - b) / (b - a), j < m, l < n.
 cheb_status cheb_matrix(const double *x, int64_t stride, int64_t m, int n, double a, double b,
                         double *T, cudaStream_t st);

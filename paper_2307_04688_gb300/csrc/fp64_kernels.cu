@@ -14,22 +14,36 @@ constexpr int kF64Cols = 32;      // output columns j of a tile
 constexpr int kF64Threads = 256;  // 64 rows x 4 column groups, 8 columns each
 constexpr int kMaxN = 64;
 
-// Mode product on a row-major [R x n] view (Section 3.2, one pagemtimes
-// step): out[j * R + r] = sum_k B[j, k] X[r, k]. A block owns 64 rows and
-// 32 output columns. X rows are staged with an odd stride so that the 64-bit
-// shared loads of consecutive rows fall in different banks; B is read as a
-// broadcast. Output stores are coalesced along r.
+// Whether slab g is skipped: the flag of its group g / per_flag is set.
+__device__ __forceinline__ bool slab_skipped(const SlabSkip &sk, int64_t g)
+{
+    return sk.flags && __ldg(sk.flags + (g / sk.per_flag) * sk.stride) != 0;
+}
+
+// Mode product on G slabs, each a row-major [R x n] view (Section 3.2, one
+// pagemtimes step per slab): out[(g m + j) R + r] = sum_k B[j, k] X[g R + r, k].
+// A block owns 64 consecutive rows of the G R and 32 output columns; a block
+// whose rows all lie in skipped slabs returns at once, and rows of skipped
+// slabs are not written. X rows are staged with an odd stride so that the
+// 64-bit shared loads of consecutive rows fall in different banks; B is read
+// as a broadcast. Output stores are coalesced along r.
 __global__ void __launch_bounds__(kF64Threads)
 modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
-                    double *__restrict__ out, int64_t R, int n, int m)
+                    double *__restrict__ out, int64_t G, int64_t R, int n, int m, const SlabSkip sk)
 {
     extern __shared__ double smem[];
     const int ns = n | 1;
     double *sX = smem;
     double *sB = smem + kF64Rows * ns;
+    const int64_t total = G * R;
     const int64_t r0 = (int64_t)blockIdx.x * kF64Rows;
     const int j0 = blockIdx.y * kF64Cols;
-    const int rows = (int)((R - r0) < kF64Rows ? (R - r0) : kF64Rows);
+    const int rows = (int)((total - r0) < kF64Rows ? (total - r0) : kF64Rows);
+    if (sk.flags) {
+        bool any = false;
+        for (int64_t g = r0 / R; g <= (r0 + rows - 1) / R; ++g) any = any || !slab_skipped(sk, g);
+        if (!any) return;     // uniform across the block
+    }
     const double *Xt = X + r0 * n;
     for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
         int rr = t / n, k = t - rr * n;
@@ -55,26 +69,33 @@ modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
         for (int q = 0; q < 8; ++q) acc[q] = fma(sB[(tj + 4 * q) * n + k], xv, acc[q]);
     }
     if (tr < rows) {
+        const int64_t rg = r0 + tr, g = rg / R, r = rg - g * R;
+        if (!slab_skipped(sk, g)) {
+            double *og = out + g * m * R + r;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = j0 + tj + 4 * q;
-            if (j < m) out[(int64_t)j * R + r0 + tr] = acc[q];
+            for (int q = 0; q < 8; ++q) {
+                const int j = j0 + tj + 4 * q;
+                if (j < m) og[(int64_t)j * R] = acc[q];
+            }
         }
     }
 }
 
-// The same product for small R (few tiles): one thread per output element, so
-// that the FP64 work spreads over the SMs instead of occupying a handful of
-// them (GB300's FP64 rate per SM is low). Same order of the k sum and the same
-// fma as the tiled kernel, hence bit-identical results.
+// The same product for small G R (few tiles): one thread per output element,
+// so that the FP64 work spreads over the SMs instead of occupying a handful
+// of them (GB300's FP64 rate per SM is low). Same order of the k sum and the
+// same fma as the tiled kernel, hence bit-identical results.
 __global__ void modeprod_f64_small_kernel(const double *__restrict__ X, const double *__restrict__ B,
-                                          double *__restrict__ out, int64_t R, int n, int m)
+                                          double *__restrict__ out, int64_t G, int64_t R, int n, int m,
+                                          const SlabSkip sk)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= R * m) return;
-    const int j = (int)(t / R);
-    const int64_t r = t - (int64_t)j * R;
-    const double *xr = X + r * n, *bj = B + (int64_t)j * n;
+    if (t >= G * R * m) return;
+    const int64_t g = t / (R * m), rem = t - g * R * m;
+    if (slab_skipped(sk, g)) return;
+    const int j = (int)(rem / R);
+    const int64_t r = rem - (int64_t)j * R;
+    const double *xr = X + (g * R + r) * n, *bj = B + (int64_t)j * n;
     double acc = 0.0;
     for (int k = 0; k < n; ++k) acc = fma(__ldg(bj + k), __ldg(xr + k), acc);
     out[t] = acc;
@@ -257,8 +278,15 @@ __global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y
 cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t R, int n, int m,
                          cudaStream_t st)
 {
-    if (R <= 0 || m <= 0) return CHEB_OK;
+    return modeprod_f64_slabs(X, B, out, 1, R, n, m, SlabSkip{}, st);
+}
+
+cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, int64_t G, int64_t R, int n, int m,
+                               const SlabSkip &skip, cudaStream_t st)
+{
+    if (G <= 0 || R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > kMaxN) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: n out of range");
+    if (skip.flags && skip.per_flag < 1) return fail(CHEB_EINVAL, "modeprod_f64: slabs per skip flag must be >= 1");
     const int ns = n | 1;
     const size_t smem = sizeof(double) * (size_t)(kF64Rows * ns + kF64Cols * n);
     static bool attr_set = false;
@@ -268,21 +296,22 @@ cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t 
                                            (int)(sizeof(double) * (kF64Rows * 65 + kF64Cols * 64))));
         attr_set = true;
     }
-    const int64_t tiles = (R + kF64Rows - 1) / kF64Rows;
+    const int64_t total = G * R;
+    const int64_t tiles = (total + kF64Rows - 1) / kF64Rows;
     if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many rows");
-    if (tiles * ((m + kF64Cols - 1) / kF64Cols) < 256 && R * m < (int64_t)1 << 26) {
-        ProfScope prof("modeprod_f64 R=" + std::to_string(R) + " n=" + std::to_string(n) +
+    if (tiles * ((m + kF64Cols - 1) / kF64Cols) < 256 && total * m < (int64_t)1 << 26) {
+        ProfScope prof("modeprod_f64 R=" + std::to_string(total) + " n=" + std::to_string(n) +
                            " m=" + std::to_string(m) + " (per element)",
                        st);
-        modeprod_f64_small_kernel<<<(unsigned)((R * m + 127) / 128), 128, 0, st>>>(X, B, out, R, n, m);
+        modeprod_f64_small_kernel<<<(unsigned)((total * m + 127) / 128), 128, 0, st>>>(X, B, out, G, R, n, m, skip);
         CHEB_CUDA_TRY(cudaGetLastError());
         return CHEB_OK;
     }
     dim3 grid((unsigned)tiles, (unsigned)((m + kF64Cols - 1) / kF64Cols));
     if (grid.y > 65535) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many columns");
-    ProfScope prof("modeprod_f64 R=" + std::to_string(R) + " n=" + std::to_string(n) +
+    ProfScope prof("modeprod_f64 R=" + std::to_string(total) + " n=" + std::to_string(n) +
                        " m=" + std::to_string(m), st);
-    modeprod_f64_kernel<<<grid, kF64Threads, smem, st>>>(X, B, out, R, n, m);
+    modeprod_f64_kernel<<<grid, kF64Threads, smem, st>>>(X, B, out, G, R, n, m, skip);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }

@@ -23,6 +23,7 @@
 // FP64-accurate iterations (polish) needs no host round trip.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -201,26 +202,6 @@ __global__ void commit_stat_kernel(const GameDev *__restrict__ insts, GameStat *
     }
 }
 
-// Transpose [rows x G] -> [G x rows] (the fit chain leaves the instance-player
-// index last; this puts it back in front).
-__global__ void transpose_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t rows, int G)
-{
-    __shared__ double tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int g0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int64_t r = r0 + k;
-        const int gg = g0 + threadIdx.x;
-        if (r < rows && gg < G) tile[k][threadIdx.x] = in[r * G + gg];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int gg = g0 + k;
-        const int64_t r = r0 + threadIdx.x;
-        if (r < rows && gg < G) out[(int64_t)gg * rows + r] = tile[threadIdx.x][k];
-    }
-}
-
 __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0, int has_u0)
 {
     const GameDev g = insts[blockIdx.y];
@@ -237,30 +218,32 @@ __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0,
 // ---------------------------------------------------------------------------
 
 // FP64 refit of every instance's Vn_new into C: the instances of a group are
-// contiguous, so the J nodal tensors of all B instances form one
-// (B J, n, ..., n) array; J rotating mode products (eq. (forcoef) along each
-// player's mode) leave the layout (l_1..l_J, B J), and a transpose restores
-// (B J, l_1..l_J).
+// contiguous, so the J nodal tensors of all B instances are G = B J slabs of
+// n^J values; J mode products per slab (eq. (forcoef) along each player's
+// mode), each moving the new mode to the slab's front, leave every slab in
+// its original mode order, the last one written straight into C. With
+// `stats`, slabs of finished instances are skipped: their coefficients stay as
+// last fitted, which is what a refit of their unchanged Vn_new would give.
+static_assert(offsetof(GameStat, done) == 0 && sizeof(GameStat) % sizeof(int) == 0, "GameStat layout");
 static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const double *Vn_new_all,
-                               double *C_all, double *tmp0, double *tmp1, cudaStream_t st)
+                               double *C_all, double *tmp0, double *tmp1, const GameStat *stats, cudaStream_t st)
 {
-    const int64_t total = (int64_t)G * NP;
     const double *M = nullptr;
     cheb_status r = dct_matrix(ctx, n, &M);
     if (r) return r;
+    SlabSkip sk;
+    if (stats) {
+        sk.flags = &stats->done;
+        sk.stride = (int64_t)(sizeof(GameStat) / sizeof(int));
+        sk.per_flag = J;
+    }
     const double *src = Vn_new_all;
     double *bufs[2] = {tmp0, tmp1};
     for (int t = 0; t < J; ++t) {
-        double *dst = bufs[t & 1];
-        if ((r = modeprod_f64(src, M, dst, total / n, n, n, st))) return r;
+        double *dst = (t == J - 1) ? C_all : bufs[t & 1];
+        if ((r = modeprod_f64_slabs(src, M, dst, G, NP / n, n, n, sk, st))) return r;
         src = dst;
     }
-    dim3 grid((unsigned)((NP + 31) / 32), (unsigned)((G + 31) / 32));
-    {
-        ProfScope prof("game_transpose", st);
-        transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, C_all, NP, G);
-    }
-    CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
 
@@ -374,7 +357,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     const unsigned copy_blocks = (unsigned)std::min<int64_t>(((int64_t)per + 255) / 256, 256);
     init_state_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, any_v0, any_u0);
     CHEB_CUDA_TRY(cudaGetLastError());
-    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, st))) return r;
+    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, nullptr, st))) return r;
 
     // ---- one iteration ----
     const unsigned node_blocks = (unsigned)((NP + 127) / 128);
@@ -401,7 +384,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
             player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
-        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, s))) return e;
+        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, s))) return e;
         {
             ProfScope prof("game_commit", s);
             commit_copy_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);

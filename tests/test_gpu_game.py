@@ -115,6 +115,28 @@ def test_batch_of_mixed_instances(ctx):
         assert rel(V[q].cpu().numpy(), ref["Vcoef"]) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_batch_instances_finishing_at_different_iterations(ctx, prec):
+    """Instances of one size class that stop at different iterations: the refit skips the
+    finished ones, so each must keep exactly the coefficients of its own last iteration, as
+    when solved alone (FP64: and as the oracle's solve)."""
+    rng = I.SplitMix64(91)
+    ps = [I.draw_game_params(rng, 3) for _ in range(5)]
+    n = 9
+    iters = [3, 40, 7, 1, 20]
+    opts = [cb.game_opts(n, tol=0.0, max_iter=k, prec=prec, polish_fp64=False) for k in iters]
+    V, u, res = cb.game_solve(ctx, ps, opts, raise_on_error=False)
+    for q in range(5):
+        assert res[q].iters == iters[q]
+        Vq, uq, rq = cb.game_solve(ctx, ps[q], opts[q], raise_on_error=False)
+        assert torch.equal(V[q], Vq[0]) and torch.equal(u[q], uq[0])
+        assert res[q].residual == rq[0].residual
+    if prec == "fp64":
+        for q in (0, 1):
+            ref = O.game_solve(ps[q], O.make_opts(n, tol=0.0, max_iter=iters[q]))
+            assert rel(V[q].cpu().numpy(), ref["Vcoef"]) < 1e-12
+
+
 def test_invalid_arguments(ctx):
     p = I.single_game_workload()
     with pytest.raises(cb.ChebError) as e:
