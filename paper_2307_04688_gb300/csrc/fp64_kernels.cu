@@ -10,8 +10,8 @@ namespace cheb {
 namespace {
 
 constexpr int kF64Rows = 64;      // rows r of a tile
-constexpr int kF64Cols = 32;      // output columns j of a tile
-constexpr int kF64Threads = 256;  // 64 rows x 4 column groups, 8 columns each
+constexpr int kF64Threads = 256;  // 64 rows x 4 column groups, Q columns each
+constexpr int kF64MaxQ = 9;       // a tile has 4 Q <= 36 output columns
 constexpr int kMaxN = 64;
 
 // Whether slab g is skipped: the flag of its group g / per_flag is set.
@@ -22,22 +22,25 @@ __device__ __forceinline__ bool slab_skipped(const SlabSkip &sk, int64_t g)
 
 // Mode product on G slabs, each a row-major [R x n] view (Section 3.2, one
 // pagemtimes step per slab): out[(g m + j) R + r] = sum_k B[j, k] X[g R + r, k].
-// A block owns 64 consecutive rows of the G R and 32 output columns; a block
+// A block owns 64 consecutive rows of the G R and 4 Q output columns (Q = the
+// smallest that covers m <= 36 in one column tile, else 8); a block
 // whose rows all lie in skipped slabs returns at once, and rows of skipped
 // slabs are not written. X rows are staged with an odd stride so that the
 // 64-bit shared loads of consecutive rows fall in different banks; B is read
 // as a broadcast. Output stores are coalesced along r.
-__global__ void __launch_bounds__(kF64Threads)
+template <int Q>
+__global__ void __launch_bounds__(kF64Threads, 4)
 modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
                     double *__restrict__ out, int64_t G, int64_t R, int n, int m, const SlabSkip sk)
 {
+    constexpr int kCols = 4 * Q;
     extern __shared__ double smem[];
     const int ns = n | 1;
     double *sX = smem;
     double *sB = smem + kF64Rows * ns;
     const int64_t total = G * R;
     const int64_t r0 = (int64_t)blockIdx.x * kF64Rows;
-    const int j0 = blockIdx.y * kF64Cols;
+    const int j0 = blockIdx.y * kCols;
     const int rows = (int)((total - r0) < kF64Rows ? (total - r0) : kF64Rows);
     if (sk.flags) {
         bool any = false;
@@ -53,27 +56,27 @@ modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
         int rr = rows + t / n, k = t % n;
         sX[rr * ns + k] = 0.0;
     }
-    for (int t = threadIdx.x; t < kF64Cols * n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < kCols * n; t += blockDim.x) {
         int jj = t / n, k = t - jj * n;
         sB[t] = (j0 + jj < m) ? B[(int64_t)(j0 + jj) * n + k] : 0.0;
     }
     __syncthreads();
     const int tr = threadIdx.x & (kF64Rows - 1);
     const int tj = threadIdx.x / kF64Rows;
-    double acc[8];
+    double acc[Q];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int q = 0; q < Q; ++q) acc[q] = 0.0;
     for (int k = 0; k < n; ++k) {
         const double xv = sX[tr * ns + k];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = fma(sB[(tj + 4 * q) * n + k], xv, acc[q]);
+        for (int q = 0; q < Q; ++q) acc[q] = fma(sB[(tj + 4 * q) * n + k], xv, acc[q]);
     }
     if (tr < rows) {
         const int64_t rg = r0 + tr, g = rg / R, r = rg - g * R;
         if (!slab_skipped(sk, g)) {
             double *og = out + g * m * R + r;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < Q; ++q) {
                 const int j = j0 + tj + 4 * q;
                 if (j < m) og[(int64_t)j * R] = acc[q];
             }
@@ -273,6 +276,21 @@ __global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y
     out[j] = (float)result;
 }
 
+template <int Q>
+cheb_status launch_f64(dim3 grid, size_t smem, cudaStream_t st, const double *X, const double *B, double *out,
+                       int64_t G, int64_t R, int n, int m, const SlabSkip &skip)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(modeprod_f64_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * (kF64Rows * 65 + 4 * Q * 64))));
+        attr_set = true;
+    }
+    modeprod_f64_kernel<Q><<<grid, kF64Threads, smem, st>>>(X, B, out, G, R, n, m, skip);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
 }  // namespace
 
 cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t R, int n, int m,
@@ -287,19 +305,14 @@ cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, in
     if (G <= 0 || R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > kMaxN) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: n out of range");
     if (skip.flags && skip.per_flag < 1) return fail(CHEB_EINVAL, "modeprod_f64: slabs per skip flag must be >= 1");
+    const int Q = m <= 4 * kF64MaxQ ? (m + 3) / 4 : 8;
+    const int cols = 4 * Q;
     const int ns = n | 1;
-    const size_t smem = sizeof(double) * (size_t)(kF64Rows * ns + kF64Cols * n);
-    static bool attr_set = false;
-    if (!attr_set) {
-        CHEB_CUDA_TRY(cudaFuncSetAttribute(modeprod_f64_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(double) * (kF64Rows * 65 + kF64Cols * 64))));
-        attr_set = true;
-    }
+    const size_t smem = sizeof(double) * (size_t)(kF64Rows * ns + cols * n);
     const int64_t total = G * R;
     const int64_t tiles = (total + kF64Rows - 1) / kF64Rows;
     if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many rows");
-    if (tiles * ((m + kF64Cols - 1) / kF64Cols) < 256 && total * m < (int64_t)1 << 26) {
+    if (tiles * ((m + cols - 1) / cols) < 256 && total * m < (int64_t)1 << 26) {
         ProfScope prof("modeprod_f64 R=" + std::to_string(total) + " n=" + std::to_string(n) +
                            " m=" + std::to_string(m) + " (per element)",
                        st);
@@ -307,13 +320,21 @@ cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, in
         CHEB_CUDA_TRY(cudaGetLastError());
         return CHEB_OK;
     }
-    dim3 grid((unsigned)tiles, (unsigned)((m + kF64Cols - 1) / kF64Cols));
+    dim3 grid((unsigned)tiles, (unsigned)((m + cols - 1) / cols));
     if (grid.y > 65535) return fail(CHEB_EUNSUPPORTED, "modeprod_f64: too many columns");
     ProfScope prof("modeprod_f64 R=" + std::to_string(total) + " n=" + std::to_string(n) +
                        " m=" + std::to_string(m), st);
-    modeprod_f64_kernel<<<grid, kF64Threads, smem, st>>>(X, B, out, G, R, n, m, skip);
-    CHEB_CUDA_TRY(cudaGetLastError());
-    return CHEB_OK;
+    switch (Q) {
+    case 1: return launch_f64<1>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 2: return launch_f64<2>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 3: return launch_f64<3>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 4: return launch_f64<4>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 5: return launch_f64<5>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 6: return launch_f64<6>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 7: return launch_f64<7>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    case 8: return launch_f64<8>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    default: return launch_f64<9>(grid, smem, st, X, B, out, G, R, n, m, skip);
+    }
 }
 
 cheb_status cheb_matrix(const double *x, int64_t stride, int64_t m, int n, double a, double b,
