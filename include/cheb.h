@@ -196,6 +196,32 @@ CHEB_API cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, cons
                            void *stream);
 
 /*
+ * cheb_eval_grid_host - cheb_eval_grid with host buffers.
+ *
+ * The same evaluation (Section 3.2) for callers whose data lives in host
+ * memory: the call copies the coefficients and the points to the device,
+ * evaluates as cheb_eval_grid does, copies the result back and returns once
+ * it is in `out` (it synchronises `stream`, so it cannot be captured into a
+ * CUDA graph). The point arrays are gathered into one page-locked context
+ * buffer and copied together.
+ *
+ *  d, n, a, b, m, prec   as in cheb_eval_grid
+ *  coeffs  host, prod(n) doubles
+ *  x       host array of d host pointers; x[s] holds m[s] doubles
+ *  out     host, prod(m) values, row-major in (j_1..j_d): doubles for
+ *          CHEB_FP64, floats for the split forms
+ * Page-locked (pinned) host memory gives asynchronous copies at the link's
+ * rate; pageable memory works but is staged by the CUDA driver. The device
+ * copies live in context-owned buffers that grow on demand (CHEB_ENOMEM if
+ * that allocation fails). Errors of the arguments are reported before any
+ * copy; a CUDA error of a copy or of the evaluation returns CHEB_ECUDA.
+ */
+CHEB_API cheb_status cheb_eval_grid_host(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                                const double *a, const double *b, const int32_t *m,
+                                const double *const *x, void *out, cheb_precision prec,
+                                void *stream);
+
+/*
  * cheb_eval_points - evaluate an interpolant at P scattered points.
  *
  * Section 3.3 (one polynomial, a different point per evaluation):

@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import (CHEB_BF16X3, CHEB_BF16X6, CHEB_FP64, CHEB_TF32X3, PRECISIONS, ChebError,
                    GameOpts, GameParams, GameResult, check, load)
 
-__all__ = ["Context", "Surrogate", "cheb_filter", "cheb_smooth", "cheb_fit", "cheb_eval_grid", "cheb_eval_points", "game_solve",
+__all__ = ["Context", "Surrogate", "cheb_filter", "cheb_smooth", "cheb_fit", "cheb_eval_grid", "cheb_eval_grid_host", "cheb_eval_points", "game_solve",
            "CHEB_FP64", "CHEB_TF32X3", "CHEB_BF16X3", "CHEB_BF16X6", "ChebError", "precision"]
 
 
@@ -159,6 +159,42 @@ def cheb_eval_grid(ctx: Context, coeffs, xs, a=None, b=None, prec="fp64", out=No
     check(load().cheb_eval_grid(ctx.handle, d, _i32(coeffs.shape), C.c_void_p(coeffs.data_ptr()),
                                 _f64(a), _f64(b), _i32(shape), ptrs, C.c_void_p(out.data_ptr()), p,
                                 _stream_ptr(stream)))
+    return out
+
+
+def _need_host(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError(f"{name} must be a CPU tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def cheb_eval_grid_host(ctx: Context, coeffs, xs, a=None, b=None, prec="fp64", out=None, stream=None):
+    """cheb_eval_grid with host (CPU) tensors in and out: the library copies the coefficients and
+    points to the device, evaluates, and copies the grid back before returning. Pinned tensors
+    (`pin_memory()`) give the fastest copies; `out` defaults to a new pinned tensor."""
+    import torch
+    _need_host(coeffs, torch.float64, "coeffs")
+    d = coeffs.dim()
+    if len(xs) != d:
+        raise ValueError("need one point array per mode")
+    for i, x in enumerate(xs):
+        _need_host(x, torch.float64, f"xs[{i}]")
+    a = [-1.0] * d if a is None else list(a)
+    b = [1.0] * d if b is None else list(b)
+    p = precision(prec)
+    shape = tuple(int(x.numel()) for x in xs)
+    dt = torch.float64 if p == CHEB_FP64 else torch.float32
+    if out is None:
+        out = torch.empty(shape, dtype=dt, pin_memory=True)
+    _need_host(out, dt, "out")
+    ptrs = (C.c_void_p * d)(*[x.data_ptr() for x in xs])
+    check(load().cheb_eval_grid_host(ctx.handle, d, _i32(coeffs.shape), C.c_void_p(coeffs.data_ptr()),
+                                     _f64(a), _f64(b), _i32(shape), ptrs, C.c_void_p(out.data_ptr()), p,
+                                     _stream_ptr(stream)))
     return out
 
 

@@ -66,6 +66,7 @@ def load():
     L.cheb_device_status.argtypes = [vp]
     L.cheb_fit.argtypes = [vp, C.c_int, ip, vp, vp, vp]
     L.cheb_eval_grid.argtypes = [vp, C.c_int, ip, vp, dp, dp, ip, C.POINTER(vp), vp, C.c_int, vp]
+    L.cheb_eval_grid_host.argtypes = [vp, C.c_int, ip, vp, dp, dp, ip, C.POINTER(vp), vp, C.c_int, vp]
     L.cheb_eval_points.argtypes = [vp, C.c_int, ip, vp, dp, dp, C.c_int64, vp, vp, C.c_int, vp]
     L.game_solve.argtypes = [vp, C.c_int32, C.POINTER(GameParams), C.POINTER(GameOpts),
                              C.POINTER(GameResult), vp]
@@ -90,7 +91,7 @@ def load():
     L.surrogate_predict.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
     for f in ("surrogate_create", "surrogate_destroy", "surrogate_params", "surrogate_loss_grad",
               "surrogate_train", "surrogate_predict", "cheb_profile", "cheb_profile_count", "cheb_profile_get", "cheb_set_tuning",
-              "cheb_tuning_report", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid",
+              "cheb_tuning_report", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid", "cheb_eval_grid_host",
               "cheb_eval_points", "game_solve", "game_paths"):
         getattr(L, f).restype = C.c_int
     _lib = L

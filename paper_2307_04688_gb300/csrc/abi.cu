@@ -238,6 +238,10 @@ cheb_status cheb_destroy(cheb_ctx *ctx)
     ctx->game.release();
     ctx->game_aux.release();
     ctx->paths.release();
+    ctx->io_in.release();
+    ctx->io_out.release();
+    if (ctx->pts_host) cudaFreeHost(ctx->pts_host);
+    if (ctx->pts_done) cudaEventDestroy(ctx->pts_done);
     if (ctx->d_error) cudaFree(ctx->d_error);
     prof_drain(ctx);
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
@@ -454,6 +458,67 @@ cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double 
         cur = R * m[mode];
         src = dst;
     }
+    return CHEB_OK;
+}
+
+cheb_status cheb_eval_grid_host(cheb_ctx *ctx, int d, const int32_t *n, const double *coeffs,
+                                const double *a, const double *b, const int32_t *m,
+                                const double *const *x, void *out, cheb_precision prec, void *stream)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    int64_t total = 0;
+    if ((st = check_shape(d, n, 64, &total))) return st;
+    if ((st = check_domain(d, a, b))) return st;
+    if (!coeffs || !out || !m || !x) return fail(CHEB_EINVAL, "null argument");
+    if (prec < CHEB_FP64 || prec > CHEB_BF16X6) return fail(CHEB_EINVAL, "bad precision");
+    int64_t out_total = 1, npts = 0;
+    for (int s = 0; s < d; ++s) {
+        if (m[s] < 1 || m[s] > 4096) return fail(CHEB_EINVAL, "m[s] must be in [1, 4096]");
+        if (!x[s]) return fail(CHEB_EINVAL, "null point array");
+        out_total *= m[s];
+        npts += m[s];
+    }
+    if (out_total > ((int64_t)1 << 34)) return fail(CHEB_EINVAL, "grid too large");
+    const size_t cbytes = sizeof(double) * (size_t)total;
+    const size_t xoff = (cbytes + 255) / 256 * 256;
+    const size_t obytes = (prec == CHEB_FP64 ? sizeof(double) : sizeof(float)) * (size_t)out_total;
+    if ((st = ctx->io_in.reserve(xoff + sizeof(double) * (size_t)npts))) return st;
+    if ((st = ctx->io_out.reserve(obytes))) return st;
+    const size_t xbytes = sizeof(double) * (size_t)npts;
+    // the staging buffer is free once the previous call's copy out of it has
+    // run (a call that failed after enqueuing it did not synchronise)
+    if (!ctx->pts_done) CHEB_CUDA_TRY(cudaEventCreateWithFlags(&ctx->pts_done, cudaEventDisableTiming));
+    CHEB_CUDA_TRY(cudaEventSynchronize(ctx->pts_done));
+    if (ctx->pts_host_bytes < xbytes) {
+        if (ctx->pts_host) cudaFreeHost(ctx->pts_host);
+        ctx->pts_host = nullptr;
+        ctx->pts_host_bytes = 0;
+        if (cudaMallocHost(&ctx->pts_host, xbytes) != cudaSuccess) {
+            ctx->pts_host = nullptr;
+            cudaGetLastError();
+            return fail(CHEB_ENOMEM, "cheb_eval_grid_host: page-locked staging of the points");
+        }
+        ctx->pts_host_bytes = xbytes;
+    }
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    uint8_t *din = static_cast<uint8_t *>(ctx->io_in.ptr);
+    std::vector<const double *> xd(d);
+    size_t off = 0;
+    for (int s = 0; s < d; ++s) {
+        std::memcpy(static_cast<uint8_t *>(ctx->pts_host) + off, x[s], sizeof(double) * (size_t)m[s]);
+        xd[s] = reinterpret_cast<const double *>(din + xoff + off);
+        off += sizeof(double) * (size_t)m[s];
+    }
+    CHEB_CUDA_TRY(cudaMemcpyAsync(din + xoff, ctx->pts_host, xbytes, cudaMemcpyHostToDevice, sm));
+    CHEB_CUDA_TRY(cudaEventRecord(ctx->pts_done, sm));
+    CHEB_CUDA_TRY(cudaMemcpyAsync(din, coeffs, cbytes, cudaMemcpyHostToDevice, sm));
+    if ((st = cheb_eval_grid(ctx, d, n, reinterpret_cast<const double *>(din), a, b, m, xd.data(), ctx->io_out.ptr,
+                             prec, stream)))
+        return st;
+    tl_ctx = ctx;
+    CHEB_CUDA_TRY(cudaMemcpyAsync(out, ctx->io_out.ptr, obytes, cudaMemcpyDeviceToHost, sm));
+    CHEB_CUDA_TRY(cudaStreamSynchronize(sm));
     return CHEB_OK;
 }
 

@@ -56,6 +56,13 @@ struct cheb_ctx {
     cheb::DevBuf game;                  // game state of one game_solve call
     cheb::DevBuf game_aux;
     cheb::DevBuf paths;                 // control coefficients of one game_paths call
+    // cheb_eval_grid_host: device copies of the host inputs and of the
+    // result, and a page-locked host buffer that gathers the point arrays
+    // into one copy
+    cheb::DevBuf io_in, io_out;
+    void *pts_host = nullptr;
+    size_t pts_host_bytes = 0;
+    cudaEvent_t pts_done = nullptr;     // the last copy out of pts_host has finished
     // tile-shape tuning (cheb_set_tuning): 0 tune on first use, 1 default
     // shapes, 2 + k force configuration k; tuned choices by shape key
     int tune_mode = 0;

@@ -122,6 +122,43 @@ def test_tensor_grid_d4_n33(ctx, big, prec):
             assert e < 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_eval_grid_host_buffers(ctx, big, prec, pinned):
+    """cheb_eval_grid_host (host coefficients, points and result; the library does the copies)
+    returns exactly what cheb_eval_grid returns on device copies of the same inputs, for pinned
+    and pageable host memory, on the full 64^4 grid."""
+    w, c, ref = big
+    ch = torch.from_numpy(np.ascontiguousarray(c))
+    xh = [torch.from_numpy(np.ascontiguousarray(g)) for g in w["grid"]]
+    if pinned:
+        ch, xh = ch.pin_memory(), [x.pin_memory() for x in xh]
+        out = None
+    else:
+        out = torch.empty((64,) * 4, dtype=torch.float64 if prec == "fp64" else torch.float32)
+    got = cb.cheb_eval_grid_host(ctx, ch, xh, prec=prec, out=out)
+    assert got.device.type == "cpu"
+    want = cb.cheb_eval_grid(ctx, dev(c), [dev(g) for g in w["grid"]], prec=prec).cpu()
+    assert torch.equal(got, want)
+    assert err(got, ref) < (1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_eval_grid_host_small_and_invalid(ctx, small):
+    """A small grid (points that fit the staging buffer of the earlier call; fewer modes), and
+    argument errors reported before any copy."""
+    w, c, G = small
+    xs = [np.linspace(-1, 1, 5), np.linspace(-0.5, 1, 3)]
+    got = cb.cheb_eval_grid_host(ctx, torch.from_numpy(np.ascontiguousarray(c)),
+                                 [torch.from_numpy(x) for x in xs], prec="fp64")
+    assert err(got.numpy(), O.eval_grid(c, xs)) < 1e-12
+    with pytest.raises(cb.ChebError):
+        cb.cheb_eval_grid_host(ctx, torch.from_numpy(np.ascontiguousarray(c)),
+                               [torch.from_numpy(x) for x in xs], a=[1.0, 0.0], b=[0.0, 1.0])
+    with pytest.raises(TypeError):
+        cb.cheb_eval_grid_host(ctx, dev(c), [torch.from_numpy(x) for x in xs])
+    ctx.device_status()
+
+
 def test_fit_d4_n33(ctx, big):
     w, c, _ = big
     a = lobatto(33)
