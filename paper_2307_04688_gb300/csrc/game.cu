@@ -224,13 +224,23 @@ __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0,
 // its original mode order, the last one written straight into C. With
 // `stats`, slabs of finished instances are skipped: their coefficients stay as
 // last fitted, which is what a refit of their unchanged Vn_new would give.
+// Large split-precision groups (`df`) refit in double-float on the FP32 pipe
+// instead (game_refit_df, relative error about 2^-47): on GB300 the FP64
+// refit was a quarter of a batched n = 33 iteration.
 static_assert(offsetof(GameStat, done) == 0 && sizeof(GameStat) % sizeof(int) == 0, "GameStat layout");
 static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const double *Vn_new_all,
-                               double *C_all, double *tmp0, double *tmp1, const GameStat *stats, cudaStream_t st)
+                               double *C_all, double *tmp0, double *tmp1, const GameStat *stats, bool df,
+                               cudaStream_t st)
 {
     const double *M = nullptr;
     cheb_status r = dct_matrix(ctx, n, &M);
     if (r) return r;
+    // double-float only where its 64-row tiles fill the GPU twice over: below
+    // that the FP64 product (one thread per output for small problems) has
+    // the shorter latency
+    const int64_t tiles = ((int64_t)G * (NP / n) + 63) / 64;
+    if (df && game_refit_df_supported(n) && tiles >= 2 * (int64_t)ctx->num_sms)
+        return game_refit_df(Vn_new_all, M, C_all, tmp0, tmp1, G, J, n, NP, stats, st);
     SlabSkip sk;
     if (stats) {
         sk.flags = &stats->done;
@@ -357,7 +367,8 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     const unsigned copy_blocks = (unsigned)std::min<int64_t>(((int64_t)per + 255) / 256, 256);
     init_state_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, any_v0, any_u0);
     CHEB_CUDA_TRY(cudaGetLastError());
-    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, nullptr, st))) return r;
+    const bool df_refit = prec != CHEB_FP64 && prec != CHEB_DF64;
+    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, nullptr, df_refit, st))) return r;
 
     // ---- one iteration ----
     const unsigned node_blocks = (unsigned)((NP + 127) / 128);
@@ -384,7 +395,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
             player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
-        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, s))) return e;
+        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, df_refit, s))) return e;
         {
             ProfScope prof("game_commit", s);
             commit_copy_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);

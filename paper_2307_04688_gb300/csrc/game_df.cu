@@ -9,7 +9,8 @@
 // compensated (two-sum), so the series w_j[k] and the value at the maximiser
 // carry relative errors of a few 1e-14 while using FP32 instructions only.
 //  - coefficients: split once per iteration into (hi, lo) pairs by
-//    game_coef_df_kernel (the refit itself stays FP64);
+//    game_coef_df_kernel (the refit of an FP64 or double-float solve stays
+//    FP64; split-precision solves refit in double-float, refit_df_kernel);
 //  - T_k of the next states by the three-term recurrence in double-float;
 //  - the contraction as in the FP64 kernel (last mode innermost), each inner
 //    dot product accumulated unnormalised (the rounding errors of the sums
@@ -21,6 +22,7 @@
 //    values in double-float. The residual is FP64.
 #include <algorithm>
 #include <cmath>
+#include <string>
 
 #include "game_internal.cuh"
 
@@ -299,7 +301,124 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
 }
 
+// ---- double-float refit (split-precision solves) ------------------------------
+// One mode of the refit (Section 3.4, Step 4: eq. (forcoef) along one mode)
+// on the FP32 pipe, the same slab-wise product as the FP64 refit:
+// out[(g n + j) R + r] = sum_k M[j, k] X[g R + r, k] over G slabs (slab g =
+// player g % J of instance g / J) of R rows, slabs of finished instances
+// skipped (stats null: none). Between the J modes the values stay
+// double-float pairs (8 bytes, like the FP64 values they replace): the first
+// mode reads FP64 values (IN_D), the last writes FP64 coefficients (OUT_D).
+// A block takes 64 rows and all 4Q >= n output columns; each thread one row
+// and Q columns, every product error-free and every sum compensated, so a
+// coefficient carries a relative error of about 2^-47 (the split forms' own
+// is above 2^-24).
+constexpr int kRfRows = 64, kRfThreads = 256;
+
+template <int Q, bool IN_D, bool OUT_D>
+__global__ void __launch_bounds__(kRfThreads, 4)
+refit_df_kernel(const void *__restrict__ Xv, const double *__restrict__ M, void *__restrict__ outv, int64_t G,
+                int64_t R, int n, const GameStat *__restrict__ stats, int J)
+{
+    extern __shared__ dfl rsm[];
+    const int ns = n | 1;
+    dfl *sX = rsm;
+    dfl *sM = rsm + kRfRows * ns;
+    const int64_t total = G * R;
+    const int64_t r0 = (int64_t)blockIdx.x * kRfRows;
+    const int rows = (int)((total - r0) < kRfRows ? (total - r0) : kRfRows);
+    if (stats) {
+        bool any = false;
+        for (int64_t g = r0 / R; g <= (r0 + rows - 1) / R; ++g) any = any || !stats[g / J].done;
+        if (!any) return;     // uniform across the block
+    }
+    for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
+        const int rr = t / n, k = t - rr * n;
+        sX[rr * ns + k] = IN_D ? df_of(static_cast<const double *>(Xv)[r0 * n + t])
+                               : static_cast<const dfl *>(Xv)[r0 * n + t];
+    }
+    for (int t = threadIdx.x; t < (kRfRows - rows) * n; t += blockDim.x) {
+        const int rr = rows + t / n, k = t % n;
+        sX[rr * ns + k] = {0.0f, 0.0f};
+    }
+    for (int t = threadIdx.x; t < 4 * Q * n; t += blockDim.x) {
+        const int jj = t / n, k = t - jj * n;
+        sM[t] = jj < n ? df_of(M[jj * n + k]) : dfl{0.0f, 0.0f};
+    }
+    __syncthreads();
+    const int tr = threadIdx.x & (kRfRows - 1);
+    const int tj = threadIdx.x / kRfRows;
+    dacc acc[Q];
+    for (int k = 0; k < n; ++k) {
+        const dfl xv = sX[tr * ns + k];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) df_mac(acc[q], sM[(tj + 4 * q) * n + k], xv);
+    }
+    if (tr < rows) {
+        const int64_t rg = r0 + tr, g = rg / R, r = rg - g * R;
+        if (!stats || !stats[g / J].done) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = tj + 4 * q;
+                if (j >= n) continue;
+                const dfl v = df_done(acc[q]);
+                const int64_t o = (g * n + j) * R + r;
+                if (OUT_D)
+                    static_cast<double *>(outv)[o] = df_val(v);
+                else
+                    static_cast<dfl *>(outv)[o] = v;
+            }
+        }
+    }
+}
+
+template <int Q>
+cheb_status refit_df_mode(const void *X, bool in_d, const double *M, void *out, bool out_d, int64_t G, int64_t R,
+                          int n, const GameStat *stats, int J, cudaStream_t st)
+{
+    const int64_t tiles = (G * R + kRfRows - 1) / kRfRows;
+    if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "refit: too many rows");
+    const size_t smem = sizeof(dfl) * (size_t)(kRfRows * (n | 1) + 4 * Q * n);
+    const unsigned grid = (unsigned)tiles;
+    if (in_d && out_d)
+        refit_df_kernel<Q, true, true><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+    else if (in_d)
+        refit_df_kernel<Q, true, false><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+    else if (out_d)
+        refit_df_kernel<Q, false, true><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+    else
+        refit_df_kernel<Q, false, false><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
 }  // namespace
+
+bool game_refit_df_supported(int n) { return n == 5 || n == 9 || n == 17 || n == 33; }
+
+cheb_status game_refit_df(const double *V, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
+                          int n, int NP, const GameStat *stats, cudaStream_t st)
+{
+    if (!game_refit_df_supported(n)) return fail(CHEB_EUNSUPPORTED, "double-float refit: n not in {5, 9, 17, 33}");
+    const void *src = V;
+    double *bufs[2] = {tmp0, tmp1};
+    ProfScope prof("game_refit_df n=" + std::to_string(n), st);
+    for (int t = 0; t < J; ++t) {
+        const bool last = t == J - 1;
+        void *dst = last ? static_cast<void *>(C) : static_cast<void *>(bufs[t & 1]);
+        const int64_t R = NP / n;
+        cheb_status r;
+        switch (n) {
+        case 5: r = refit_df_mode<2>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
+        case 9: r = refit_df_mode<3>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
+        case 17: r = refit_df_mode<5>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
+        default: r = refit_df_mode<9>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
+        }
+        if (r) return r;
+        src = dst;
+    }
+    return CHEB_OK;
+}
 
 cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st)
 {

@@ -152,6 +152,13 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
 // ---- double-float player update (game_df.cu): coefficient split + update ----
 cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st);
 
+// ---- double-float refit of G = B J slabs (game_df.cu), for split-precision
+// solves: C = V with eq. (forcoef) applied along each of the J modes; slabs of
+// finished instances skipped when `stats` is given. n in {5, 9, 17, 33}.
+bool game_refit_df_supported(int n);
+cheb_status game_refit_df(const double *V, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
+                          int n, int NP, const GameStat *stats, cudaStream_t st);
+
 // ---- split-precision player update (game_tc.cu) ----
 size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec);
 void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws);

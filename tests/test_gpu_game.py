@@ -137,6 +137,24 @@ def test_batch_instances_finishing_at_different_iterations(ctx, prec):
             assert rel(V[q].cpu().numpy(), ref["Vcoef"]) < 1e-12
 
 
+@pytest.mark.parametrize("n,count", [(33, 8), (17, 24), (9, 81), (17, 1)])
+def test_split_refit_is_the_fp64_fit_of_the_nodal_values(ctx, n, count):
+    """The coefficients a split-precision solve returns are the fit (eq. (forcoef) along every
+    mode, the oracle's FP64 DCT-I) of the nodal values it returns. Large groups (here 8 n = 33,
+    24 n = 17 or 81 n = 9 instances: over 300 tiles of 64 rows) refit in double-float on the
+    FP32 pipe, a single instance in FP64; both to 1e-13."""
+    rng = I.SplitMix64(5 + n + count)
+    ps = [I.draw_game_params(rng, 3) for _ in range(count)]
+    o = cb.game_opts(n, tol=0.0, max_iter=3, prec="bf16x6", polish_fp64=False)
+    Vn = [torch.empty((3, n ** 3), dtype=torch.float64, device="cuda") for _ in range(count)]
+    V, u, res = cb.game_solve(ctx, ps, [o] * count, Vn=Vn, raise_on_error=False)
+    for q in sorted({0, count - 1}):
+        assert res[q].iters == 3
+        for i in range(3):
+            ref = O.fit_nd(Vn[q][i].cpu().numpy().reshape(n, n, n))
+            assert rel(V[q][i].cpu().numpy().reshape(n, n, n), ref) < 1e-13
+
+
 def test_invalid_arguments(ctx):
     p = I.single_game_workload()
     with pytest.raises(cb.ChebError) as e:
