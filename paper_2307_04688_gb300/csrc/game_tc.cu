@@ -22,9 +22,13 @@
 //  - tcgen05.mma accumulates the split products of a chunk in TMEM (FP32);
 //  - the epilogue reads TMEM, multiplies by T_{k_b}(x_b(j)) (kept in
 //    registers) and writes w_j[k_i] to shared memory;
-//  - after the last chunk, one thread per node maximises over its control
-//    (Newton in FP32 from the previous control, the value at the maximiser in
-//    FP64) and writes the new control, value and the FP64 residual.
+//  - after the last chunk, one thread per node of the lower 128 maximises
+//    over its control (Newton in FP32 from the previous control, the value at
+//    the maximiser in double-float and FP64) and writes the new control, value
+//    and the FP64 residual, while the upper 128 threads run the next tile's
+//    prologue (A operand, T_{k_b} rows staged in shared memory, first B
+//    copies, first MMA); the first thread of the upper half issues every bulk
+//    copy and MMA.
 #include <algorithm>
 #include <cstdio>
 #include <string>

@@ -37,7 +37,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for f in ("cheb_create", "cheb_destroy", "cheb_last_error", "cheb_fit", "cheb_eval_grid",
-              "cheb_eval_points", "game_solve", "cheb_device_status", "cheb_version"):
+              "cheb_eval_grid_host", "cheb_eval_points", "game_solve", "cheb_device_status", "cheb_version"):
         assert f in names
 
 
@@ -53,3 +53,9 @@ def test_argument_errors_without_gpu(lib):
     assert b"context" in lib.cheb_last_error()
     h = C.c_void_p()
     assert lib.cheb_create(None, 0) == 1
+    # the host-buffer evaluation checks its context before touching any buffer
+    m = (C.c_int32 * 2)(4, 4)
+    a = (C.c_double * 2)(-1.0, -1.0)
+    b = (C.c_double * 2)(1.0, 1.0)
+    assert lib.cheb_eval_grid_host(None, 2, n, None, a, b, m, None, None, 0, None) == 1
+    assert b"context" in lib.cheb_last_error()
