@@ -38,26 +38,43 @@ namespace game {
 // device helpers
 // ---------------------------------------------------------------------------
 
-// g_l(p, u) = (1/m) sum_{l' != l} K[l][l'] (p_l' - p_l) - c_l p_l + beta_l u_l
-__device__ __forceinline__ double dynamics(const GameDev &g, int l, const double *p, double ul)
-{
-    double coup = 0.0;
-    for (int t = 0; t < g.J; ++t)
-        if (t != l) coup += g.K[l * g.J + t] * (p[t] - p[l]);
-    return coup * g.minv - g.c[l] * p[l] + g.beta[l] * ul;
-}
 
+// The next states of every node (grid: node blocks x instances):
+// p_l + h g_l(p, u) with g_l(p, u) = (1/m) sum_{l' != l} K[l][l'] (p_l' - p_l)
+// - c_l p_l + beta_l u_l (Section 2.1), mapped to the reference coordinate.
+// The loops run over the fixed maximum of 4 players with guards, so that the
+// node's coordinates stay in registers (a by-value copy of the descriptor with
+// runtime-indexed arrays put ~560 bytes per thread in local memory); pbar as
+// in node_coords.
 __global__ void next_state_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats)
 {
-    const GameDev g = insts[blockIdx.y];
+    const GameDev &g = insts[blockIdx.y];
     if (stats[blockIdx.y].done) return;
+    const int J = g.J, n = g.n, NP = g.NP;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.NP) return;
-    double xr[4], pb[4];
-    node_coords(g, j, xr, pb);
-    for (int l = 0; l < g.J; ++l) {
-        const double q = pb[l] + g.h * dynamics(g, l, pb, g.u[l * g.NP + j]);
-        g.X[l * g.NP + j] = 2.0 * q / g.P_M - 1.0;
+    if (j >= NP) return;
+    const double P_M = g.P_M;
+    double pb[4] = {0.0, 0.0, 0.0, 0.0};
+    int rem = j;
+#pragma unroll
+    for (int s = 3; s >= 0; --s) {
+        if (s < J) {
+            const int k = rem % n;
+            rem /= n;
+            pb[s] = 0.5 * P_M * (g.nodes[k] + 1.0);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (l < J) {
+            double coup = 0.0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (t < J && t != l) coup += g.K[l * J + t] * (pb[t] - pb[l]);
+            const double dyn = coup * g.minv - g.c[l] * pb[l] + g.beta[l] * g.u[l * NP + j];
+            const double q = pb[l] + g.h * dyn;
+            g.X[l * NP + j] = 2.0 * q / P_M - 1.0;
+        }
     }
 }
 
