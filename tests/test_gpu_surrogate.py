@@ -54,21 +54,6 @@ def test_gradients_match_oracle(ctx, dims):
     net.close()
 
 
-def test_oracle_gradient_against_finite_differences():
-    dims = [3, 6, 4, 2]
-    rng = np.random.default_rng(2)
-    p = rng.standard_normal(O.mlp_param_count(dims)) * 0.5
-    X = rng.standard_normal((5, 3))
-    T = rng.standard_normal((5, 2))
-    _, g = O.mlp_loss_grad(dims, p, X, T)
-    h = 1e-6
-    for i in range(0, p.size, 7):
-        e = np.zeros_like(p)
-        e[i] = h
-        num = (O.mlp_loss_grad(dims, p + e, X, T)[0] - O.mlp_loss_grad(dims, p - e, X, T)[0]) / (2 * h)
-        assert abs(num - g[i]) < 1e-8 * max(1.0, abs(g[i]))
-
-
 def test_training_reduces_loss(ctx):
     rng = np.random.default_rng(4)
     S, F, Ov = 4096, 8, 64

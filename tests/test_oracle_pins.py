@@ -376,3 +376,69 @@ def test_game_paths_of_symmetric_players_coincide():
     assert np.abs(pp[:, :, 0] - pp[:, :, 2]).max() < 1e-13
     assert np.abs(up[:, :, 0] - up[:, :, 2]).max() < 1e-13
     assert np.abs(pp[:, :, 0] - pp[:, :, 1]).max() > 1e-3
+
+
+# ---- the MLP oracle (learned warm start) -------------------------------------------------------
+
+def test_mlp_oracle_gelu_identities():
+    """GELU(z) = z Phi(z): GELU(z) - GELU(-z) = z (Phi(z) + Phi(-z) = 1), GELU(0) = 0, GELU'(0) =
+    1/2, GELU(z) -> z for large z and -> 0 for very negative z; GELU' against central
+    differences of GELU."""
+    assert O.gelu(0.0) == 0.0
+    assert abs(O.gelu_grad(0.0) - 0.5) < 1e-15
+    for z in (-3.0, -1.2, -0.3, 0.25, 0.9, 2.7):
+        assert abs(O.gelu(z) - O.gelu(-z) - z) < 1e-15
+        h = 1e-5
+        num = (O.gelu(z + h) - O.gelu(z - h)) / (2 * h)
+        assert abs(num - O.gelu_grad(z)) < 1e-9
+    assert abs(O.gelu(12.0) - 12.0) < 1e-12 and abs(O.gelu(-12.0)) < 1e-12
+
+
+def test_mlp_oracle_single_layer_is_affine_least_squares():
+    """One layer (no activation): forward = X W^T + b, and the mean-squared-error gradient is the
+    linear least-squares one, dW = 2/(B m) (Y - T)^T X, db = 2/(B m) sum_b (Y - T)."""
+    rng = np.random.default_rng(4)
+    n_in, n_out, B = 5, 3, 7
+    W = rng.standard_normal((n_out, n_in))
+    b = rng.standard_normal(n_out)
+    p = np.concatenate([W.ravel(), b])
+    X = rng.standard_normal((B, n_in))
+    T = rng.standard_normal((B, n_out))
+    Y = X @ W.T + b
+    assert np.abs(O.mlp_forward([n_in, n_out], p, X) - Y).max() < 1e-13
+    loss, g = O.mlp_loss_grad([n_in, n_out], p, X, T)
+    R = Y - T
+    assert abs(loss - np.mean(R ** 2)) < 1e-13
+    s = 2.0 / (B * n_out)
+    assert np.abs(g[:W.size].reshape(n_out, n_in) - s * R.T @ X).max() < 1e-13
+    assert np.abs(g[W.size:] - s * R.sum(axis=0)).max() < 1e-13
+
+
+def test_mlp_oracle_gradient_against_finite_differences():
+    """The full back-propagated gradient (GELU hidden layers) against central differences of the
+    loss."""
+    dims = [3, 6, 4, 2]
+    rng = np.random.default_rng(2)
+    p = rng.standard_normal(O.mlp_param_count(dims)) * 0.5
+    X = rng.standard_normal((5, 3))
+    T = rng.standard_normal((5, 2))
+    _, g = O.mlp_loss_grad(dims, p, X, T)
+    h = 1e-6
+    for i in range(0, p.size, 7):
+        e = np.zeros_like(p)
+        e[i] = h
+        num = (O.mlp_loss_grad(dims, p + e, X, T)[0] - O.mlp_loss_grad(dims, p - e, X, T)[0]) / (2 * h)
+        assert abs(num - g[i]) < 1e-8 * max(1.0, abs(g[i]))
+
+
+def test_mlp_oracle_first_adam_step_is_a_signed_step():
+    """At t = 1 the bias-corrected moments are g and g^2, so Adam moves every weight by
+    lr g / (|g| + eps): lr sign(g) up to eps."""
+    rng = np.random.default_rng(6)
+    w0 = rng.standard_normal(11)
+    g = rng.standard_normal(11)
+    w, m, v = w0.copy(), np.zeros(11), np.zeros(11)
+    lr, eps = 1e-3, 1e-12
+    O.adam_step(w, g, m, v, lr, 0.9, 0.999, eps, 1)
+    assert np.abs(w - (w0 - lr * g / (np.abs(g) + eps))).max() < 1e-15
+    assert np.abs(m - 0.1 * g).max() < 1e-15 and np.abs(v - 0.001 * g * g).max() < 1e-15
