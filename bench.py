@@ -117,7 +117,7 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
-# capture (profiles/modeprod_tc_bf16x6_R262144_n33_m64.md), valid only while
+# capture of that kernel on this workload, valid only while
 # the kernel source is the one that was profiled (sha256 prefix below).
 PROFILED_TRAFFIC = {
     ("modeprod_tc R=262144 n=33 m=64 x=f32", "bf16x6"): ("cd5024a2916dd4c0", 41817088),

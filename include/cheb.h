@@ -95,6 +95,18 @@ CHEB_API const char *cheb_version(void);
  * (CHEB_ETIMEOUT). Returns CHEB_OK if no kernel reported a failure. */
 CHEB_API cheb_status cheb_device_status(cheb_ctx *ctx);
 
+/* Bound of the device-side waits of the tensor-core grid evaluation
+ * (cheb_eval_grid and cheb_eval_points in a split form): a CTA that has waited
+ * `cycles` SM clock cycles for a bulk copy or an MMA gives up, records
+ * CHEB_ETIMEOUT in the context's device error word (see cheb_device_status),
+ * still waits with the default bound for the copies and MMAs it started, frees
+ * its tensor memory and returns; the output of that call is then undefined.
+ * cycles >= 0; 0 makes every such wait give up at once (for testing the
+ * failure path). CHEB_WAIT_LIMIT_DEFAULT (2^32 cycles, about 2 s) is the
+ * default. Not a paper concept: failure detection of the device code. */
+#define CHEB_WAIT_LIMIT_DEFAULT 4294967296LL
+CHEB_API cheb_status cheb_set_wait_limit(cheb_ctx *ctx, int64_t cycles);
+
 /* Kernel timing. With profiling on, the library brackets every kernel it
  * launches with CUDA events on the launch stream (the stream the caller
  * passed) and accumulates, per kernel name, the launch count and the summed
@@ -260,13 +272,23 @@ CHEB_API cheb_status cheb_eval_points(cheb_ctx *ctx, int d, const int32_t *n, co
  * GPU that loads it until the process exits). Its address is looked up the
  * first time the call runs on a device; make that first call before any
  * stream capture. All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller. Bounded device waits that run
- * out are recorded only in the array's own error word (not reported).
+ * race and must be serialised by the caller. A bounded device wait that runs
+ * out (CHEB_ETIMEOUT) is recorded in the array's own error word, which every
+ * call clears when it starts: read it with cheb_eval_grid_noalloc_status.
  */
 CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, const double *coeffs,
                                             const double *a, const double *b, const int32_t *m,
                                             const double *const *x, float *out,
                                             cheb_precision prec, void *stream);
+
+/* Device status of the last cheb_eval_grid_noalloc call on the current device:
+ * waits for `stream` (the stream of that call), reads the error word of the
+ * library's fixed array and returns CHEB_OK, or CHEB_ETIMEOUT if a bounded
+ * device wait of that call ran out (its output is then undefined). The word is
+ * cleared by the next cheb_eval_grid_noalloc call, not by this one. Allocates
+ * nothing; returns CHEB_EINVAL if cheb_eval_grid_noalloc never ran on the
+ * current device. */
+CHEB_API cheb_status cheb_eval_grid_noalloc_status(void *stream);
 
 /* ------------------------------------------------------------------------
  * The J-player pollution game (Section 2, linear-quadratic specification,
@@ -404,6 +426,14 @@ CHEB_API cheb_status surrogate_params(cheb_mlp *net, float *get, const float *se
  * (device, parameter count floats, optional). Synchronous when loss != NULL. */
 CHEB_API cheb_status surrogate_loss_grad(cheb_ctx *ctx, cheb_mlp *net, const float *X, const float *T,
                                          int32_t B, float *loss, float *grad, void *stream);
+
+/* One Adam step (b1 = 0.9, b2 = 0.999, eps = 1e-8, bias-corrected with the
+ * network's step count t, which this call increments) on the FP32 master
+ * weights: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). grad: device,
+ * parameter count floats in the surrogate_params layout, or NULL for the
+ * gradient of the last surrogate_loss_grad call. Stream-ordered. */
+CHEB_API cheb_status surrogate_adam_step(cheb_ctx *ctx, cheb_mlp *net, const float *grad, float lr, void *stream);
 
 /* Train on S samples: X device FP64 (row i at X + i * x_stride, n_in values),
  * Y device FP64 targets (row stride y_stride, n_out values). Inputs and

@@ -76,6 +76,12 @@ class Context:
         1 default shapes, 2 + k force configuration k (4 * chunk index + CTAs per SM)."""
         check(load().cheb_set_tuning(self._h, int(mode)))
 
+    def set_wait_limit(self, cycles: int = _lib.CHEB_WAIT_LIMIT_DEFAULT) -> None:
+        """Bound, in SM cycles, of the device-side waits of the split-form grid and point
+        evaluation (default 2^32); a wait that runs out reports CHEB_ETIMEOUT through
+        device_status(). 0 makes every such wait give up at once."""
+        check(load().cheb_set_wait_limit(self._h, int(cycles)))
+
     def tuning_report(self) -> str:
         """One line per tuned shape: key, chosen configuration, time of each one tried."""
         buf = C.create_string_buffer(1 << 16)
@@ -350,6 +356,18 @@ class Surrogate:
                                          int(X.shape[0]), C.byref(loss), C.c_void_p(g.data_ptr()),
                                          _stream_ptr(stream)))
         return float(loss.value), g
+
+    def adam_step(self, grad=None, lr: float = 1e-3, stream=None) -> None:
+        """One Adam step on the FP32 master weights with `grad` (float32 CUDA tensor of
+        param_count() entries) or, if None, the gradient of the last loss_grad call."""
+        import torch
+        if grad is not None:
+            _need_cuda(grad, torch.float32, "grad")
+            if grad.numel() != self.param_count():
+                raise ValueError("wrong gradient size")
+        check(load().surrogate_adam_step(self.ctx.handle, self._h,
+                                         None if grad is None else C.c_void_p(grad.data_ptr()), float(lr),
+                                         _stream_ptr(stream)))
 
     def train(self, X, Y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, stream=None):
         """X (S x n_in) and Y (S x n_out, any row stride) float64 CUDA tensors; returns the loss per epoch."""

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "CHEB_OK", 1: "CHEB_EINVAL", 2: "CHEB_ENOMEM", 3: "CHEB_ECUDA
                 5: "CHEB_ESTALL", 6: "CHEB_ETIMEOUT", 7: "CHEB_EUNSUPPORTED"}
 CHEB_FP64, CHEB_TF32X3, CHEB_BF16X3, CHEB_BF16X6 = range(4)
 CHEB_DF64 = 4
+CHEB_WAIT_LIMIT_DEFAULT = 1 << 32
 PRECISIONS = {"fp64": CHEB_FP64, "tf32x3": CHEB_TF32X3, "bf16x3": CHEB_BF16X3, "bf16x6": CHEB_BF16X6,
               "df64": CHEB_DF64}
 
@@ -81,6 +82,7 @@ def load():
     L.game_paths.argtypes = [vp, C.POINTER(GameParams), C.POINTER(GameOpts), vp, C.c_int64, vp, C.c_int64, vp,
                              vp, vp]
     L.cheb_set_tuning.argtypes = [vp, C.c_int]
+    L.cheb_set_wait_limit.argtypes = [vp, C.c_int64]
     L.cheb_tuning_report.argtypes = [vp, C.c_char_p, C.c_int64]
     L.surrogate_create.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(vp)]
     L.surrogate_destroy.argtypes = [vp]
@@ -89,8 +91,9 @@ def load():
     L.surrogate_train.argtypes = [vp, vp, vp, C.c_int64, vp, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
                                   C.c_float, C.c_uint64, C.POINTER(C.c_float), vp]
     L.surrogate_predict.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
+    L.surrogate_adam_step.argtypes = [vp, vp, vp, C.c_float, vp]
     for f in ("surrogate_create", "surrogate_destroy", "surrogate_params", "surrogate_loss_grad",
-              "surrogate_train", "surrogate_predict", "cheb_profile", "cheb_profile_count", "cheb_profile_get", "cheb_set_tuning",
+              "surrogate_train", "surrogate_predict", "surrogate_adam_step", "cheb_profile", "cheb_profile_count", "cheb_profile_get", "cheb_set_tuning", "cheb_set_wait_limit",
               "cheb_tuning_report", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid", "cheb_eval_grid_host",
               "cheb_eval_points", "game_solve", "game_paths"):
         getattr(L, f).restype = C.c_int

@@ -264,6 +264,15 @@ cheb_status cheb_device_status(cheb_ctx *ctx)
     return CHEB_OK;
 }
 
+cheb_status cheb_set_wait_limit(cheb_ctx *ctx, int64_t cycles)
+{
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    if (cycles < 0) return fail(CHEB_EINVAL, "cheb_set_wait_limit: cycles must be >= 0");
+    ctx->wait_limit = (long long)cycles;
+    return CHEB_OK;
+}
+
 cheb_status cheb_profile(cheb_ctx *ctx, int enable)
 {
     cheb_status st = check_ctx(ctx);

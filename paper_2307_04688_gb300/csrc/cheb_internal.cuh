@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,40 @@ cheb_status cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (expr);                                             \
         if (e_ != cudaSuccess) return ::cheb::cuda_fail(e_, #expr);          \
     } while (0)
+
+// Bound of a device-side wait in SM cycles (about 2 s at 2 GHz); must equal
+// the kernels' own default (tc_common.cuh) and CHEB_WAIT_LIMIT_DEFAULT.
+constexpr long long kDefaultWaitCycles = 1ll << 32;
+
+// One-time set-up per device (kernel attributes such as the dynamic shared
+// memory limit apply to the device that is current when they are set): the
+// first call on a device runs `init` with that device current and caches the
+// int it produces; later calls on the same device return the cached value.
+// Thread-safe. A failed `init` is retried by the next call.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+    std::mutex mu;
+    bool set[kMaxDevices] = {};
+    int val[kMaxDevices] = {};
+};
+
+template <class Init>
+cheb_status per_device_once(PerDevice &pd, Init init, int *out)
+{
+    int dev = 0;
+    CHEB_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(CHEB_EUNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(pd.mu);
+    if (!pd.set[dev]) {
+        int v = 0;
+        const cheb_status st = init(&v);
+        if (st != CHEB_OK) return st;
+        pd.val[dev] = v;
+        pd.set[dev] = true;
+    }
+    if (out) *out = pd.val[dev];
+    return CHEB_OK;
+}
 
 // A device buffer owned by the context that only grows.
 struct DevBuf {
@@ -68,6 +103,7 @@ struct cheb_ctx {
     int tune_mode = 0;
     std::map<std::string, std::pair<int, std::string>> game_tune;
     int *d_error = nullptr;             // device error word written by bounded waits
+    long long wait_limit = cheb::kDefaultWaitCycles;   // SM cycles a main-loop device wait may take
     // kernel timing (cheb_profile): events around every library launch
     bool prof_on = false;
     struct ProfEvent {
@@ -143,7 +179,8 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
 // `num_sms` the SM count of the current device.
 cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
                             int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st,
-                            const double *xpts = nullptr, double ta = -1.0, double tb = 1.0);
+                            const double *xpts = nullptr, double ta = -1.0, double tb = 1.0,
+                            long long wait_limit = kDefaultWaitCycles);
 
 // Evaluation at the Lobatto nodes E[k, l] = cos(pi l k / N), cached per n.
 cheb_status node_eval_matrix(cheb_ctx *ctx, int n, const double **out);

@@ -280,12 +280,13 @@ template <int Q>
 cheb_status launch_f64(dim3 grid, size_t smem, cudaStream_t st, const double *X, const double *B, double *out,
                        int64_t G, int64_t R, int n, int m, const SlabSkip &skip)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDevice attr;
+    cheb_status r = per_device_once(attr, [](int *) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(modeprod_f64_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * (kF64Rows * 65 + 4 * Q * 64))));
-        attr_set = true;
-    }
+        return CHEB_OK;
+    }, nullptr);
+    if (r) return r;
     modeprod_f64_kernel<Q><<<grid, kF64Threads, smem, st>>>(X, B, out, G, R, n, m, skip);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;

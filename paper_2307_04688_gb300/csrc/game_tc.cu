@@ -340,9 +340,13 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const int stage = c & 1;
         const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
         const int N = S::TCOL + kis * S::NBP;
-        if (!mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) *abort_flag = 1;
-        ld_phase ^= 1u << stage;
-        pending &= ~(1u << stage);
+        // a copy whose wait gave up stays pending: the exit path waits for it
+        if (mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) {
+            ld_phase ^= 1u << stage;
+            pending &= ~(1u << stage);
+        } else {
+            *abort_flag = 1;
+        }
         tc_fence_after();
         const uint32_t idesc = make_idesc(F::FMT, kTile, N);
         const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + stage * S::CHUNK_BYTES);
@@ -443,12 +447,16 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             const int buf = c & 1;
             const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
             if (tid == kProducer && c + 1 < S::NCH) issue_mma(c + 1);
-            if (!mbar_wait_bounded(&bars[2 + buf], (mma_phase >> buf) & 1u, err)) *abort_flag = 1;
-            mma_phase ^= 1u << buf;
-            mma_out &= ~(1u << buf);
+            if (mbar_wait_bounded(&bars[2 + buf], (mma_phase >> buf) & 1u, err)) {
+                mma_phase ^= 1u << buf;
+                mma_out &= ~(1u << buf);
+            } else {
+                *abort_flag = 1;
+            }
             tc_fence_after();
             // the B stage of chunk c is free again: prefetch chunk c + 2 into it
-            if (tid == kProducer && c + 2 < S::NCH) {
+            // (not while a copy into it is still pending after a timeout)
+            if (tid == kProducer && c + 2 < S::NCH && !(pending & (1u << buf))) {
                 mbar_arrive_expect_tx(&bars[buf], S::CHUNK_BYTES);
                 bulk_g2s(sB + buf * S::CHUNK_BYTES, bsrc + (size_t)(c + 2) * S::CHUNK_BYTES, S::CHUNK_BYTES,
                          &bars[buf]);
@@ -603,8 +611,8 @@ cheb_status max_ctas(int *out)
 {
     using S = Shape<FORM, NN, CH>;
     auto kern = game_player_tc_kernel<FORM, NN, CH>;
-    static int cached = 0;
-    if (!cached) {
+    static PerDevice cache;
+    return per_device_once(cache, [kern](int *v) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
@@ -613,10 +621,9 @@ cheb_status max_ctas(int *out)
         const int regs = std::max(8, (fa.numRegs + 7) / 8 * 8);
         int k = (int)(228 * 1024 / (S::SMEM + 1024));
         k = std::min({k, 65536 / (regs * kThreads), 512 / S::TMEM_ALLOC, 2048 / kThreads, 3});
-        cached = std::max(1, k);
-    }
-    *out = cached;
-    return CHEB_OK;
+        *v = std::max(1, k);
+        return CHEB_OK;
+    }, out);
 }
 
 template <int FORM, int NN, int CH>

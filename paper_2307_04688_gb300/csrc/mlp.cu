@@ -103,6 +103,7 @@ gemm_bf16_kernel(const GemmArgs g)
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = make_idesc(1, kBM, kBN);
     uint32_t phase = 0;
+    bool mma_pending = false;     // MMAs issued and not yet waited for (timeout path)
     const int nk = (g.K + kBK - 1) / kBK;
     for (int kb = 0; kb < nk; ++kb) {
         stage_operand(sA, g.A, g.sa_m, g.sa_k, g.M, m0, kb * kBK, g.K, tid);
@@ -121,8 +122,13 @@ gemm_bf16_kernel(const GemmArgs g)
             }
             mma_commit(&bar);
         }
-        if (!mbar_wait_bounded(&bar, phase, g.err)) abort_flag = 1;
-        phase ^= 1u;
+        mma_pending = true;
+        if (mbar_wait_bounded(&bar, phase, g.err)) {
+            phase ^= 1u;
+            mma_pending = false;
+        } else {
+            abort_flag = 1;
+        }
         tc_fence_after();
         __syncthreads();   // the operands may be overwritten by the next chunk
         if (abort_flag) break;
@@ -153,6 +159,7 @@ gemm_bf16_kernel(const GemmArgs g)
             }
         }
     }
+    if (mma_pending) mbar_wait_bounded(&bar, phase, g.err);   // full bound before TMEM is freed
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -165,11 +172,12 @@ cheb_status gemm(const GemmArgs &a, cudaStream_t st)
     dim3 grid((unsigned)((a.N + kBN - 1) / kBN), (unsigned)((a.M + kBM - 1) / kBM));
     // 24 KB of otherwise unused dynamic shared memory caps residency at four
     // CTAs per SM, so that their TMEM accumulators (128 columns each) fit in 512
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    cheb_status r = per_device_once(attr, [](int *) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * 1024));
-        attr = true;
-    }
+        return CHEB_OK;
+    }, nullptr);
+    if (r) return r;
     ProfScope prof("mlp_gemm_bf16", st);
     gemm_bf16_kernel<<<grid, kThreads, 24 * 1024, st>>>(a);
     CHEB_CUDA_TRY(cudaGetLastError());
@@ -552,6 +560,24 @@ CHEB_API cheb_status surrogate_loss_grad(cheb_ctx *ctx, cheb_mlp *net, const flo
         CHEB_CUDA_TRY(cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
         CHEB_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    return CHEB_OK;
+}
+
+CHEB_API cheb_status surrogate_adam_step(cheb_ctx *ctx, cheb_mlp *net, const float *grad, float lr, void *stream)
+{
+    cheb_status r = check_net(ctx, net);
+    if (r) return r;
+    if (!(lr > 0)) return fail(CHEB_EINVAL, "surrogate_adam_step: lr must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    net->adam_t += 1;
+    const float c1 = 1.0f - std::pow(b1, (float)net->adam_t), c2 = 1.0f - std::pow(b2, (float)net->adam_t);
+    {
+        ProfScope prof("mlp_adam", st);
+        adam_kernel<<<blocks_for(net->nparam), 256, 0, st>>>(net->nparam, net->w, grad ? grad : net->grad, net->m,
+                                                            net->v, lr, b1, b2, eps, c1, c2);
+    }
+    CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
 

@@ -34,7 +34,6 @@ namespace {
 constexpr size_t kScratchBytes = 64ull << 20;   // FP32 intermediates
 constexpr size_t kTmatBytes = 1ull << 20;       // FP64 T matrices
 constexpr size_t kTotalBytes = kScratchBytes + kTmatBytes + 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kTotalBytes];
 
@@ -152,5 +151,26 @@ extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, 
         cur = R * m[mode];
         src = dst;
     }
+    return CHEB_OK;
+}
+
+extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc_status(void *stream)
+{
+    tl_ctx = nullptr;
+    int device = 0;
+    CHEB_CUDA_TRY(cudaGetDevice(&device));
+    if (device < 0 || device >= kMaxDevices) return fail(CHEB_EUNSUPPORTED, "device ordinal too large");
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mutex);
+        if (g_slots[device].ready) base = g_slots[device].base;
+    }
+    if (!base) return fail(CHEB_EINVAL, "cheb_eval_grid_noalloc_status: no call ran on this device");
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    const int *err = reinterpret_cast<const int *>(base + kScratchBytes + kTmatBytes);
+    int v = 0;
+    CHEB_CUDA_TRY(cudaStreamSynchronize(sm));
+    CHEB_CUDA_TRY(cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) return fail((cheb_status)v, "cheb_eval_grid_noalloc: a device-side wait ran out of time");
     return CHEB_OK;
 }

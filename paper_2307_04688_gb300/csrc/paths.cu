@@ -175,11 +175,12 @@ extern "C" CHEB_API cheb_status game_paths(cheb_ctx *ctx, const cheb_game_params
     P.h = opts->h;
     P.P_M = opts->P_M;
     P.U_M = opts->U_M;
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    cheb_status ra = per_device_once(attr, [](int *) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(game_paths_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+        return CHEB_OK;
+    }, nullptr);
+    if (ra) return ra;
     const int64_t grid = std::min<int64_t>(K, (int64_t)ctx->num_sms * 8);
     ProfScope prof("game_paths J=" + std::to_string(J) + " n=" + std::to_string(n), st);
     game_paths_kernel<<<(unsigned)grid, kThreads, smem, st>>>(P);

@@ -54,15 +54,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete, giving up after about
-// 2^32 SM cycles (~2 s). Returns false on timeout and records
-// CHEB_ETIMEOUT (6) in the context's device error word `err`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+// Default bound of a device-side wait: 2^32 SM cycles (about 2 s).
+constexpr long long kWaitCycles = 1ll << 32;
+
+// Wait for phase `parity` of `bar` to complete, giving up once `limit` SM
+// cycles have passed (the limit is checked before every try, so a limit of 0
+// gives up at once). Returns false on timeout and records CHEB_ETIMEOUT (6)
+// in the device error word `err`. A caller that gives up must still wait, with
+// the default bound, for the copies and MMAs that signal `bar` before its CTA
+// frees TMEM or exits.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  long long limit = kWaitCycles)
 {
     const long long t0 = clock64();
     for (uint32_t it = 0; it < (1u << 28); ++it) {
+        if (clock64() - t0 >= limit) break;
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > (1ll << 32)) break;
     }
     atomicCAS(err, 0, 6);
     return false;

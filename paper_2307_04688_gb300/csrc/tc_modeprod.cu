@@ -86,6 +86,7 @@ struct Params {
     int Np;        // N = m padded to 16
     int tmem_cols; // power of two >= max(32, Np)
     int *err;
+    long long wait_limit;   // SM cycles a main-loop wait may take (exit-path waits use the default)
 };
 
 __host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -173,8 +174,14 @@ modeprod_tc_kernel(const Params P)
 
     // B splits, once per CTA: rows j < Np, chunks c < KC. With xpts given,
     // row j is T_0..T_{n-1} at x~_j = (2 x_j - ta - tb) / (tb - ta) by the
-    // three-term recurrence in double-float (one row per thread, then split).
+    // three-term recurrence in double-float (one row per thread, then split);
+    // the points are caller input, written before the chain started, so this
+    // overlaps the previous kernel. A given B may come from the previous
+    // kernel in the stream (the T-matrix kernel): it is read only after the
+    // wait for that kernel's completion and memory.
     if (P.B) {
+        griddep_launch_dependents();
+        griddep_wait();
         for (int t = tid; t < Np * KC; t += kThreads) {
             const int j = t / KC, c = t - j * KC;
             float v[E];
@@ -231,10 +238,11 @@ modeprod_tc_kernel(const Params P)
             }
         }
     }
-    // everything above is independent of the previous kernel in the stream;
-    // from here on X (its output) is read
-    griddep_launch_dependents();
-    griddep_wait();
+    // from here on X (the previous kernel's output) is read
+    if (!P.B) {
+        griddep_launch_dependents();
+        griddep_wait();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -251,6 +259,7 @@ modeprod_tc_kernel(const Params P)
     uint32_t load_phase = 0;     // bit b: parity of the next completion of load buffer b
     uint32_t load_pending = 0;   // bit b: a copy into buffer b is in flight
     uint32_t mma_phase = 0;
+    uint32_t mma_pending = 0;    // the tile's MMAs were issued and not yet waited for
     int64_t tile = blockIdx.x;
     if (tid == 0 && tile < ntiles && tile_full(tile)) issue_load(tile, 0);
     if (tile < ntiles && tile_full(tile)) load_pending |= 1u;
@@ -271,9 +280,13 @@ modeprod_tc_kernel(const Params P)
         const int rows = (int)((P.R - tile * kTileM) < kTileM ? (P.R - tile * kTileM) : kTileM);
         const XT *xs;
         if (load_pending & (1u << buf)) {
-            if (!mbar_wait_bounded(&bars[buf], (load_phase >> buf) & 1u, P.err)) *abort_flag = 1;
-            load_phase ^= 1u << buf;
-            load_pending &= ~(1u << buf);
+            // a copy whose wait gave up stays pending: the exit path waits for it
+            if (mbar_wait_bounded(&bars[buf], (load_phase >> buf) & 1u, P.err, P.wait_limit)) {
+                load_phase ^= 1u << buf;
+                load_pending &= ~(1u << buf);
+            } else {
+                *abort_flag = 1;
+            }
             xs = reinterpret_cast<const XT *>(sX + buf * stage_bytes);
         } else {
             // ragged last tile: plain loads straight from global memory
@@ -335,8 +348,13 @@ modeprod_tc_kernel(const Params P)
             }
             mma_commit(&bars[2]);
         }
-        if (!mbar_wait_bounded(&bars[2], mma_phase, P.err)) *abort_flag = 1;
-        mma_phase ^= 1;
+        mma_pending = 1;
+        if (mbar_wait_bounded(&bars[2], mma_phase, P.err, P.wait_limit)) {
+            mma_phase ^= 1;
+            mma_pending = 0;
+        } else {
+            *abort_flag = 1;
+        }
         tc_fence_after();
         // epilogue: rows 32*quarter + lane, column chunks ehalf, ehalf + 2, ...
         {
@@ -387,9 +405,10 @@ modeprod_tc_kernel(const Params P)
         __syncthreads();
         if (*abort_flag) break;
     }
-    // drain copies still in flight (abort path), then free TMEM
+    // drain copies and MMAs still in flight (abort path, full bound), then free TMEM
     for (int b = 0; b < 2; ++b)
         if (load_pending & (1u << b)) mbar_wait_bounded(&bars[b], (load_phase >> b) & 1u, P.err);
+    if (mma_pending) mbar_wait_bounded(&bars[2], mma_phase, P.err);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -422,21 +441,21 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
     const size_t smem = a_bytes + b_bytes + kMaxTail * kMaxM * sizeof(float) + kStages * stage + 64;
     if (smem > 227 * 1024) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: tile does not fit in shared memory");
     auto kern = modeprod_tc_kernel<FORM, XT>;
-    static bool attr_done = false;
-    if (!attr_done) {
+    // kernel attributes once per device; CTAs per SM from the shared-memory
+    // budget (the occupancy query reports one CTA here although two fit),
+    // capped by TMEM columns, threads and the registers per thread
+    static PerDevice once;
+    int regs = 0;
+    cheb_status ra = per_device_once(once, [kern](int *v) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
-        attr_done = true;
-    }
-    // CTAs per SM from the shared-memory budget (the occupancy query reports
-    // one CTA here although two fit), capped by TMEM columns and threads.
-    static int regs = 0;
-    if (!regs) {
         cudaFuncAttributes fa;
         CHEB_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-        regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
-    }
+        *v = std::max(1, (fa.numRegs + 7) / 8 * 8);
+        return CHEB_OK;
+    }, &regs);
+    if (ra) return ra;
     int per_sm = (int)(228 * 1024 / (smem + 1024));
     per_sm = std::max(1, std::min({per_sm, 2048 / kThreads, 65536 / (regs * kThreads)}));
     while (per_sm > 1 && per_sm * P.tmem_cols > 512) --per_sm;
@@ -463,7 +482,7 @@ cheb_status launch(const Params &P0, int num_sms, cudaStream_t st)
 
 cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *out, int64_t R, int n,
                             int m, cheb_precision prec, int *err, int num_sms, cudaStream_t st,
-                            const double *xpts, double ta, double tb)
+                            const double *xpts, double ta, double tb, long long wait_limit)
 {
     if (R <= 0 || m <= 0) return CHEB_OK;
     if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
@@ -482,6 +501,7 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
     P.n = n;
     P.m = m;
     P.err = err;
+    P.wait_limit = wait_limit;
     switch (prec) {
     case CHEB_BF16X3:
         return x_f64 ? launch<CHEB_BF16X3, double>(P, num_sms, st) : launch<CHEB_BF16X3, float>(P, num_sms, st);
@@ -498,34 +518,8 @@ cheb_status modeprod_tc(cheb_ctx *ctx, const void *X, int x_f64, const double *B
                         int64_t R, int n, int m, cheb_precision prec, cudaStream_t st,
                         const double *xpts, double ta, double tb)
 {
-    if (R <= 0 || m <= 0) return CHEB_OK;
-    if (n < 1 || n > 64) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: n must be in [1, 64]");
-    if (m > kMaxM) return fail(CHEB_EUNSUPPORTED, "modeprod_tc: m must be <= 256");
-    if ((reinterpret_cast<uintptr_t>(X) & 15) != 0)
-        return fail(CHEB_EINVAL, "modeprod_tc: X must be 16-byte aligned");
-    Params P{};
-    if (!B && !xpts) return fail(CHEB_EINVAL, "modeprod_tc: need B or the points");
-    P.X = X;
-    P.B = B;
-    P.xpts = xpts;
-    P.xscale = 2.0 / (tb - ta);
-    P.xshift = -(ta + tb) / (tb - ta);
-    P.out = out;
-    P.R = R;
-    P.n = n;
-    P.m = m;
-    P.err = ctx->d_error;
-    const int sms = ctx->num_sms;
-    switch (prec) {
-    case CHEB_BF16X3:
-        return x_f64 ? launch<CHEB_BF16X3, double>(P, sms, st) : launch<CHEB_BF16X3, float>(P, sms, st);
-    case CHEB_BF16X6:
-        return x_f64 ? launch<CHEB_BF16X6, double>(P, sms, st) : launch<CHEB_BF16X6, float>(P, sms, st);
-    case CHEB_TF32X3:
-        return x_f64 ? launch<CHEB_TF32X3, double>(P, sms, st) : launch<CHEB_TF32X3, float>(P, sms, st);
-    default:
-        return fail(CHEB_EINVAL, "modeprod_tc: not a split precision");
-    }
+    return modeprod_tc_raw(X, x_f64, B, out, R, n, m, prec, ctx->d_error, ctx->num_sms, st, xpts, ta, tb,
+                           ctx->wait_limit);
 }
 
 }  // namespace cheb

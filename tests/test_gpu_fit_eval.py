@@ -262,3 +262,33 @@ def test_k_tail_shapes(ctx, prec):
         refp = O.eval_points(cp, P, a, b)
         outp = cb.cheb_eval_points(ctx, dev(cp), dev(P), a, b, prec=prec)
         assert err(outp, refp) < 8 * split_bound(prec, d, cp, refp)
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x3"])
+def test_bounded_wait_timeout_reports_and_recovers(ctx, small, prec):
+    """Failure detection without a GPU fault: with the wait limit at 0 every bounded wait of
+    the split mode products gives up at once, records CHEB_ETIMEOUT in the context's error
+    word, drains its copies and MMAs with the default bound and returns; device_status()
+    reports it and clears it, and with the default limit back the same call is correct."""
+    w, c, _ = small
+    g = w["grid"][0]
+    ref = O.eval_grid(c, [g, g])
+    ctx.device_status()                                   # start from a clean error word
+    try:
+        ctx.set_wait_limit(0)
+        out = cb.cheb_eval_grid(ctx, dev(c), [dev(g), dev(g)], prec=prec)
+        torch.cuda.synchronize()
+        with pytest.raises(cb.ChebError) as ei:
+            ctx.device_status()
+        assert ei.value.status == cb._lib.CHEB_ETIMEOUT
+    finally:
+        ctx.set_wait_limit()
+    ctx.device_status()                                   # cleared by the read above
+    out = cb.cheb_eval_grid(ctx, dev(c), [dev(g), dev(g)], prec=prec).double().cpu().numpy()
+    ctx.device_status()
+    assert err(out, ref) <= split_bound(prec, 2, c, ref)
+
+
+def test_wait_limit_rejects_negative(ctx):
+    with pytest.raises(cb.ChebError):
+        ctx.set_wait_limit(-1)

@@ -331,3 +331,45 @@ def test_split_polish_modes_reach_tol(ctx, polish):
     assert r.status == 0 and r.residual < 1e-10 and r.iters > r.iters_split > 0
     Vf, _, _ = cb.game_solve(ctx, p, cb.game_opts(9, tol=1e-10, max_iter=20000, prec="fp64"))
     assert rel(V[0].cpu().numpy(), Vf[0].cpu().numpy()) < 1e-6
+
+
+def _node(opts, J, j):
+    import ctypes
+    pb, xr = np.empty(J), np.empty(J)
+    O.lib().orc_game_node(ctypes.byref(opts), J, int(j), pb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          xr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return pb, xr
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x3"])
+def test_mixed_size_split_batch_sampled_nodes_match_oracle(ctx, prec):
+    """The batched split path at its real shape: one game_solve over 4 n = 9, 4 n = 17 and
+    6 n = 33 instances (interleaved in the batch; the n = 33 group is large enough for the
+    double-float refit and its own tuned tile shape). Two solves, R - 1 and R passes, give
+    the GPU's iterate r = R - 1 and the pass from it; at sampled nodes of every instance and
+    every player, the oracle's Steps 1-3 from the GPU's iterate R - 1 (its coefficients and
+    controls) must give the GPU's control and value of iterate R (same bounds as the
+    single-instance sampled test)."""
+    sizes = [9, 17, 33, 9, 33, 17, 33, 9, 33, 17, 33, 9, 33, 17]
+    rng_p = I.SplitMix64(77)
+    ps = [I.draw_game_params(rng_p, 3) for _ in sizes]
+    R = 3
+    o1 = [cb.game_opts(n, tol=0.0, max_iter=R - 1, prec=prec, polish_fp64=False) for n in sizes]
+    o2 = [cb.game_opts(n, tol=0.0, max_iter=R, prec=prec, polish_fp64=False) for n in sizes]
+    V1, u1, r1 = cb.game_solve(ctx, ps, o1, raise_on_error=False)
+    V2, u2, r2 = cb.game_solve(ctx, ps, o2, raise_on_error=False)
+    assert all(r.iters == R - 1 for r in r1) and all(r.iters == R for r in r2)
+    assert all(r.iters_split == R for r in r2)
+    rng = np.random.default_rng(3)
+    tol_v = 50 * (U_FORM[prec] + 2.0 ** -20)
+    for q, n in enumerate(sizes):
+        C1, U1 = V1[q].cpu().numpy(), u1[q].cpu().numpy()
+        C2, U2 = V2[q].cpu().numpy(), u2[q].cpu().numpy()
+        opts = O.make_opts(n, tol=0.0, max_iter=R)
+        for j in rng.choice(n ** 3, 3, replace=False):
+            pb, xr = _node(opts, 3, j)
+            for i in range(3):
+                us, vs, inside, conc = O.game_node_update(ps[q], opts, i, pb, U1[:, j], C1[i])
+                v_gpu = O.eval_direct(C2[i].reshape(n, n, n), xr)
+                assert abs(us - U2[i, j]) < 1e-5, (q, n, int(j), i, us, U2[i, j])
+                assert abs(vs - v_gpu) < tol_v * max(1.0, abs(vs)), (q, n, int(j), i, vs, v_gpu)

@@ -2,10 +2,12 @@
 call cudaMalloc (a host framework owning all device memory in its own pool, or
 a hot path where cudaMalloc/cudaFree would synchronise the device).
 
-Its result must match the ordinary cheb_eval_grid (which allocates context
-workspaces) within the split-form tolerance of the other tests, on two calls
-in a row (the scratch array keeps the previous call's contents). This file is
-named to be collected last, and passes alone in a fresh process as well.
+Its result must match the CPU oracle's FP64 evaluation within the split-form
+bound of the other tests, and the ordinary cheb_eval_grid (which allocates
+context workspaces) within the same bound, on two calls in a row (the scratch
+array keeps the previous call's contents), with cheb_eval_grid_noalloc_status
+reporting no timed-out device wait. This file is named to be collected last,
+and passes alone in a fresh process as well.
 """
 import ctypes as C
 
@@ -39,35 +41,69 @@ def lib():
     vp, ip, dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)
     L.cheb_eval_grid_noalloc.argtypes = [C.c_int, ip, vp, dp, dp, ip, C.POINTER(vp), vp, C.c_int, vp]
     L.cheb_eval_grid_noalloc.restype = C.c_int
+    L.cheb_eval_grid_noalloc_status.argtypes = [vp]
+    L.cheb_eval_grid_noalloc_status.restype = C.c_int
+    import oracle as O
+    O.build()
     return L
 
 
-@pytest.mark.parametrize("prec_name", ["bf16x6", "tf32x3", "bf16x3"])
-def test_noalloc_matches_cheb_eval_grid_twice(lib, prec_name):
-    import paper_2307_04688_gb300 as cb
+def _cases():
+    """(coefficients, points per mode) on [-1, 1]^d: the d=4 n=33 64^4 workload, a ragged
+    d=3 case, d=1, d=5 with odd n and m (odd m[s] n[s] offsets of the later T matrices and
+    odd intermediate sizes), and points outside [-1, 1]."""
     from paper_2307_04688_gb300 import inputs as I
+    w = I.tensor_grid_workload()
+    out = [(w["coeffs"], list(w["grid"]))]
+    rng = np.random.default_rng(5)
+    out.append((rng.standard_normal((7, 17, 5)), [rng.uniform(-1, 1, k) for k in (4, 200, 45)]))
+    out.append((rng.standard_normal(33), [rng.uniform(-1, 1, 129)]))
+    out.append((rng.standard_normal((3, 5, 7, 9, 11)) * 0.5, [rng.uniform(-1, 1, k) for k in (5, 3, 7, 13, 9)]))
+    out.append((rng.standard_normal((9, 17)), [rng.uniform(-1.3, 1.3, 31), rng.uniform(-1.2, 1.2, 33)]))
+    return out
+
+
+def _bound(prec_name, c, xs, ref):
+    """Tolerance of the split-form tests, d * u * kappa, with kappa = max over the grid of
+    sum_k |c_k| prod_s |T_{k_s}(x_s)| over max|f| (= sum|c| / max|f| on [-1, 1], where
+    |T_k| <= 1; larger for points outside). u as in test_gpu_fit_eval.split_bound."""
+    u = {"bf16x3": 3 * 2.0 ** -18, "bf16x6": 2.0 ** -24, "tf32x3": 3 * 2.0 ** -22}[prec_name] + 4 * 2.0 ** -24
+    if max(np.abs(x).max() for x in xs) <= 1.0:
+        mag = np.abs(c).sum()
+    else:
+        acc = np.abs(c)
+        for s, x in enumerate(xs):
+            V = np.abs(np.polynomial.chebyshev.chebvander(x, c.shape[s] - 1))    # |T_k(x_j)|
+            acc = np.tensordot(V, acc, axes=([1], [s]))
+            acc = np.moveaxis(acc, 0, s)
+        mag = acc.max()
+    return c.ndim * u * mag / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec_name", ["bf16x6", "tf32x3", "bf16x3"])
+def test_noalloc_matches_oracle_and_cheb_eval_grid_twice(lib, prec_name):
+    import oracle as O
+    import paper_2307_04688_gb300 as cb
     prec = cb.precision(prec_name)
     ctx = cb.Context(0)
-    # the d=4, n=33 coefficient tensor on a 64^4 grid, and a ragged d=3 case
-    w = I.tensor_grid_workload()
-    cases = [(torch.from_numpy(w["coeffs"]).cuda(), [torch.from_numpy(g).cuda() for g in w["grid"]])]
-    rng = np.random.default_rng(5)
-    c3 = torch.from_numpy(rng.standard_normal((7, 17, 5))).cuda()
-    cases.append((c3, [torch.from_numpy(rng.uniform(-1, 1, k)).cuda() for k in (130 % 129 + 3, 200, 45)]))
-    for c, xs in cases:
-        ref = cb.cheb_eval_grid(ctx, c, xs, prec=prec_name)
-        cn = c.cpu().numpy()
-        refn = ref.double().cpu().numpy()
-        # tolerance of the split-form tests: d * u * kappa (see test_gpu_fit_eval.split_bound)
-        u = {"bf16x3": 3 * 2.0 ** -18, "bf16x6": 2.0 ** -24, "tf32x3": 3 * 2.0 ** -22}[prec_name] + 4 * 2.0 ** -24
-        tol = c.dim() * u * np.abs(cn).sum() / np.abs(refn).max()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for cn, xn in _cases():
+        c = torch.from_numpy(np.ascontiguousarray(cn)).cuda()
+        xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in xn]
+        orc = O.eval_grid(cn, xn)                      # FP64 oracle, nested mode products
+        ours = cb.cheb_eval_grid(ctx, c, xs, prec=prec_name).double().cpu().numpy()
+        tol = _bound(prec_name, cn, xn, orc)
         for call in range(2):
-            out = torch.full(ref.shape, float("nan"), dtype=torch.float32, device="cuda")
+            out = torch.full(orc.shape, float("nan"), dtype=torch.float32, device="cuda")
             st = _noalloc(lib, c, xs, prec, out)
             assert st == 0, lib.cheb_last_error()
-            torch.cuda.synchronize()
-            e = float((out.double() - ref.double()).abs().max() / ref.double().abs().max())
-            assert e <= tol, (call, e, tol)
+            assert lib.cheb_eval_grid_noalloc_status(stream) == 0, lib.cheb_last_error()
+            got = out.double().cpu().numpy()
+            scale = np.abs(orc).max()
+            e_orc = float(np.abs(got - orc).max() / scale)
+            e_sib = float(np.abs(got - ours).max() / scale)
+            assert e_orc <= tol, (cn.shape, call, e_orc, tol)
+            assert e_sib <= 2 * tol, (cn.shape, call, e_sib, tol)
     ctx.close()
 
 
