@@ -117,11 +117,10 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
-# capture of that kernel on this workload, valid only while
-# the kernel source is the one that was profiled (sha256 prefix below).
-PROFILED_TRAFFIC = {
-    ("modeprod_tc R=262144 n=33 m=64 x=f32", "bf16x6"): ("cd5024a2916dd4c0", 41817088),
-}
+# capture of that kernel on this workload, valid only while the kernel's source
+# file is the one that was profiled (sha256 prefix below).
+PROFILED_TRAFFIC = {}
+KERNEL_SOURCE = {"modeprod_tc": "tc_modeprod.cu", "modepair_tc": "tc_modepair.cu"}
 
 
 def measured_traffic(kernel_name, form):
@@ -129,10 +128,30 @@ def measured_traffic(kernel_name, form):
     ent = PROFILED_TRAFFIC.get((kernel_name, form))
     if ent is None:
         return None
-    src = os.path.join(ROOT, "paper_2307_04688_gb300", "csrc", "tc_modeprod.cu")
+    src = os.path.join(ROOT, "paper_2307_04688_gb300", "csrc", KERNEL_SOURCE[kernel_name.split()[0]])
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     return ent[1] if sha == ent[0] else None
+
+
+def launch_bytes(name, evals):
+    """Bytes of one launch of a grid-evaluation kernel, from its profile name:
+    (algorithmic, issued). Issued = its input read once + its FP32 output written
+    once. Algorithmic counts only what the evaluation itself must move (the FP64
+    coefficient tensor read once, the FP32 grid values written once): the
+    intermediates between mode products are not part of the method's traffic."""
+    kv = dict(t.split("=") for t in name.split()[1:])
+    xb = 8 if kv.get("x") == "f64" else 4
+    if name.startswith("modepair_tc"):
+        U = int(kv["U"])
+        na, nb = (int(v) for v in kv["n"].split("x"))
+        ma, mb = (int(v) for v in kv["m"].split("x"))
+        inb, outb = xb * U * na * nb, 4 * U * ma * mb
+    else:
+        R, n_, m_ = int(kv["R"]), int(kv["n"]), int(kv["m"])
+        inb, outb = xb * R * n_, 4 * R * m_
+    alg = (inb if xb == 8 else 0) + (outb if outb == 4 * evals else 0)
+    return alg, inb + outb
 
 
 def dist_setup(n_gpus):
@@ -298,15 +317,15 @@ def run_ours(args):
     _, prof = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec=form, out=out), nprof, 1, profile=True)
     launches_per_step = sum(v[0] for v in prof.values()) / nprof
 
-    # roofline of the dominant kernel (largest summed time); its name carries R, n, m
+    # roofline: the dominant kernel (largest summed time), with the algorithmic bytes of
+    # the method (FP64 coefficients read once, FP32 grid values written once), and the
+    # whole evaluation against the same bytes
     hbm, bf16, src = peaks()
     dom_name, (dom_n, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    kv = dict(t.split("=") for t in dom_name.split()[1:])
-    R, n_, m_ = int(kv["R"]), int(kv["n"]), int(kv["m"])
-    in_bytes = 8 if kv.get("x") == "f64" else 4
-    alg_bytes = in_bytes * R * n_ + 4 * R * m_          # X read once, output written once (FP32)
+    alg_bytes, issued_bytes = launch_bytes(dom_name, evals)
     per_launch_ms = dom_ms / dom_n
     traffic = measured_traffic(dom_name, form)
+    alg_eval = 4 * evals + 8 * c_np.size
     # FP64 path on the same grid (the comparison the metric names)
     out64 = torch.empty((64,) * 4, dtype=torch.float64, device="cuda")
     ms64, prof64 = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec="fp64", out=out64),
@@ -391,9 +410,14 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                          "peak_source": src,
                          "algorithmic_bytes_per_launch": alg_bytes,
+                         "issued_bytes_per_launch": issued_bytes,
                          "per_launch_ms": per_launch_ms,
-                         "note": "dominant kernel = one mode product; algorithmic bytes = its input "
-                                 "rows read once + its FP32 output written once"},
+                         "whole_evaluation": {"algorithmic_bytes": alg_eval, "ms": ms,
+                                              "achieved": alg_eval / (ms * 1e-3) / 1e9,
+                                              "frac": alg_eval / (ms * 1e-3) / 1e9 / hbm},
+                         "note": "algorithmic bytes: the FP64 coefficient tensor read once and the FP32 "
+                                 "grid values written once (intermediates excluded); issued: the launch's "
+                                 "own input read once and output written once"},
             "kernel_times_ms_per_step": {k: v[1] / nprof for k, v in prof.items()},
             "gpu_launches": launches_per_step,
             "clocks": clocks,

@@ -292,3 +292,39 @@ def test_bounded_wait_timeout_reports_and_recovers(ctx, small, prec):
 def test_wait_limit_rejects_negative(ctx):
     with pytest.raises(cb.ChebError):
         ctx.set_wait_limit(-1)
+
+
+def abs_kappa(c, xs, a=None, b=None):
+    """max over the grid of sum_k |c_k| prod_s |T_{k_s}(x~_s)| (= sum|c| on [-1, 1]^d)."""
+    acc = np.abs(c)
+    for s, x in enumerate(xs):
+        xr = x if a is None else (2 * x - a[s] - b[s]) / (b[s] - a[s])
+        V = np.abs(np.polynomial.chebyshev.chebvander(xr, c.shape[s] - 1))
+        acc = np.moveaxis(np.tensordot(V, acc, axes=([1], [s])), 0, s)
+    return float(acc.max())
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("shape,m", [
+    ((17, 18, 34, 9), (40, 17, 33, 5)),       # K tails of 1 and 2 columns in both products; ragged tiles
+    ((33, 33, 33, 33), (130, 64, 100, 3)),    # m_a > 128 in the first pair, m_b = 3 in the second
+    ((5, 64, 64, 2), (3, 128, 1, 9)),         # m_b = 128 (four MMA 2 pieces), n_a = 64, m_a = 1
+    ((9, 2, 3, 4, 33, 17), (11, 3, 2, 5, 7, 64)),   # d = 6: three fused pairs, the middle one with P, Q > 1
+])
+def test_fused_mode_pairs(ctx, shape, m, prec):
+    """Even d with the split forms runs the mode pairs (0, 1), (2, 3), ... in fused launches
+    (both products of a pair in one CTA). Shapes that exercise the K tails, ragged tiles of
+    four units, padded rows and columns of both MMAs, and points outside the domain, against
+    the oracle within d u_form kappa (kappa from |T| on the actual points)."""
+    rng = np.random.default_rng(sum(shape) + sum(m))
+    d = len(shape)
+    c = rng.standard_normal(shape)
+    a = rng.uniform(-2, 0, d)
+    b = a + rng.uniform(0.5, 3, d)
+    xs = [rng.uniform(a[s] - 0.05 * (b[s] - a[s]), b[s] + 0.05 * (b[s] - a[s]), m[s]) for s in range(d)]
+    ref = O.eval_grid(c, xs, a, b)
+    out = cb.cheb_eval_grid(ctx, dev(c), [dev(x) for x in xs], a, b, prec=prec)
+    e = err(out, ref)
+    u = {"bf16x3": 3 * 2.0 ** -18, "bf16x6": 2.0 ** -24, "tf32x3": 3 * 2.0 ** -22}[prec] + 4 * 2.0 ** -24
+    tol = d * u * abs_kappa(c, xs, a, b) / np.abs(ref).max()
+    assert e < tol, (e, tol)

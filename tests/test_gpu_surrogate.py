@@ -114,7 +114,7 @@ def _inputs(dims, regime, seed, count):
 
 
 @pytest.mark.parametrize("regime", ["positive", "mixed"])
-@pytest.mark.parametrize("dims", [[8, 32, 32, 20], [8, 256, 256, 300], [3, 16, 5], [8, 130, 129, 33]])
+@pytest.mark.parametrize("dims", [[8, 32, 32, 20], [8, 256, 256, 300], [3, 16, 5], [8, 130, 130, 33]])
 def test_forward_and_gradient_entries_match_oracle(ctx, dims, regime):
     """Every output and every gradient entry within twice its first-order bound (the factor
     covers second-order terms)."""
