@@ -154,6 +154,39 @@ def launch_bytes(name, evals):
     return alg, inb + outb
 
 
+def measure_lib_peaks(torch):
+    """Dense GEMM rates of the library (cuBLAS through torch.matmul) on this GPU, best of 5
+    timed with CUDA events: FP64 (DGEMM 4096^3), TF32 (FP32 8192^3 with TF32 tensor cores
+    allowed) and FP32 on the CUDA cores (SGEMM 4096^3, TF32 off). They are the denominators
+    of the FP64-pipe, TF32 and FP32-pipe rooflines (MEASURED_PEAKS.json has HBM and BF16)."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for key, dt, N, tf32 in (("fp64_tflops", torch.float64, 4096, False),
+                             ("tf32_tflops", torch.float32, 8192, True),
+                             ("fp32_tflops", torch.float32, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(N, N, dtype=dt, device="cuda")
+        b = torch.randn(N, N, dtype=dt, device="cuda")
+        c = torch.empty(N, N, dtype=dt, device="cuda")
+        torch.matmul(a, b, out=c)
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        out[key] = 2.0 * N ** 3 / best / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul best of 5, CUDA events: DGEMM 4096^3, TF32 8192^3, SGEMM 4096^3 (2 N^3 flops)"
+    return out
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,6 +359,13 @@ def run_ours(args):
     per_launch_ms = dom_ms / dom_n
     traffic = measured_traffic(dom_name, form)
     alg_eval = 4 * evals + 8 * c_np.size
+    # 2 FLOP per multiply-add of the d mode products (modes d-1, ..., 0 in turn)
+    fp64_flops = 0
+    cur = c_np.size
+    for s_ in range(3, -1, -1):
+        fp64_flops += 2 * cur // c_np.shape[s_] * 64 * c_np.shape[s_]
+        cur = cur // c_np.shape[s_] * 64
+    lib_peaks = measure_lib_peaks(torch)
     # FP64 path on the same grid (the comparison the metric names)
     out64 = torch.empty((64,) * 4, dtype=torch.float64, device="cuda")
     ms64, prof64 = timed(lambda: cb.cheb_eval_grid(ctx, c, xs, prec="fp64", out=out64),
@@ -339,6 +379,34 @@ def run_ours(args):
         forms[f] = {"ms": msf, "evals_per_s": world * evals / (msf * 1e-3),
                     "max_norm_err_vs_fp64_path": float(((o.double() - out64).abs().max() /
                                                         out64.abs().max()).item())}
+    # d = 2, n = 17 (the plain method in FP64): nodal values (the oracle's direct
+    # summation of the seeded coefficients) -> cheb_fit -> 129^2 grid + 10,000
+    # points; one step = the three calls
+    import oracle as O
+    O.build()
+    w1 = I.small_fit_workload()
+    lob = np.cos(np.pi * np.arange(17) / 16)
+    G1 = torch.from_numpy(O.eval_grid(w1["coeffs"], [lob, lob])).cuda()
+    g1 = [torch.from_numpy(np.ascontiguousarray(g)).cuda() for g in w1["grid"]]
+    P1 = torch.from_numpy(np.ascontiguousarray(w1["points"])).cuda()
+    c1 = torch.empty_like(G1)
+    o1g = torch.empty((129, 129), dtype=torch.float64, device="cuda")
+    o1p = torch.empty(P1.shape[0], dtype=torch.float64, device="cuda")
+
+    def cfg1_step():
+        cb.cheb_fit(ctx, G1, c1)
+        cb.cheb_eval_grid(ctx, c1, g1, prec="fp64", out=o1g)
+        cb.cheb_eval_points(ctx, c1, P1, prec="fp64", out=o1p)
+
+    ms1, _ = timed(cfg1_step, max(5, args.steps), 3)
+    ref1g = O.eval_grid(w1["coeffs"], list(w1["grid"]))
+    ref1p = O.eval_points(w1["coeffs"], w1["points"])
+    config1 = {"workload": "d=2 n=17 fit of the nodal values + 129x129 grid + 10,000 points, FP64 (seed 0)",
+               "ms_per_step": ms1, "evals_per_s": world * (129 * 129 + P1.shape[0]) / (ms1 * 1e-3),
+               "coef_err": float(np.abs(c1.cpu().numpy() - w1["coeffs"]).max() / np.abs(w1["coeffs"]).max()),
+               "grid_err_vs_oracle": float(np.abs(o1g.cpu().numpy() - ref1g).max() / np.abs(ref1g).max()),
+               "points_err_vs_oracle": float(np.abs(o1p.cpu().numpy() - ref1p).max() / np.abs(ref1p).max())}
+
     # the FP64 fit of the 33^4 nodal tensor (cheb_fit)
     nod = out64[:33, :33, :33, :33].contiguous()
     msfit, _ = timed(lambda: cb.cheb_fit(ctx, nod), 5, 2)
@@ -402,9 +470,16 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "error": {"max_norm_vs_fp64_gpu_path": err_vs_fp64},
             "fp64_path": {"ms_per_step": ms64, "evals_per_s": world * evals / (ms64 * 1e-3),
-                          "speedup_of_split": ms64 / ms},
+                          "speedup_of_split": ms64 / ms,
+                          "roofline": {"bound": "fp64", "achieved": fp64_flops / (ms64 * 1e-3) / 1e12,
+                                       "peak": lib_peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                       "frac": fp64_flops / (ms64 * 1e-3) / 1e12 / lib_peaks["fp64_tflops"],
+                                       "peak_source": "measured (DGEMM, this run)",
+                                       "algorithmic_flops": fp64_flops}},
             "forms": forms,
             "fit_fp64_33^4": {"ms": msfit},
+            "config1": config1,
+            "peaks_measured": lib_peaks,
             "game": game,
             "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
