@@ -423,39 +423,6 @@ cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double 
             if (m[s] > 256) return fail(CHEB_EUNSUPPORTED, "split forms support m[s] <= 256");
     }
     cudaStream_t sm = static_cast<cudaStream_t>(stream);
-    // Split forms with an even number of modes: the mode pairs (0, 1), (2, 3),
-    // ... each in one fused launch (the intermediate between the two products
-    // of a pair never leaves the SM), when every pair fits the fused kernel.
-    if (prec != CHEB_FP64 && d % 2 == 0 && d >= 4) {
-        bool fits = true;
-        size_t cap = 0;
-        int64_t P = 1, Q = total;
-        for (int t = 0; t < d / 2; ++t) {
-            const int a0 = 2 * t, a1 = 2 * t + 1;
-            Q /= (int64_t)n[a0] * n[a1];
-            fits = fits && modepair_tc_fits(n[a0], n[a1], m[a0], m[a1], t == 0, Q, prec);
-            P *= (int64_t)m[a0] * m[a1];
-            if (t < d / 2 - 1) cap = std::max(cap, sizeof(float) * (size_t)(P * Q));
-        }
-        if (fits) {
-            if ((st = ctx->ws[0].reserve(cap))) return st;
-            if ((st = ctx->ws[1].reserve(cap))) return st;
-            const void *src = coeffs;
-            P = 1;
-            Q = total;
-            for (int t = 0; t < d / 2; ++t) {
-                const int a0 = 2 * t, a1 = 2 * t + 1;
-                Q /= (int64_t)n[a0] * n[a1];
-                float *dst = (t == d / 2 - 1) ? static_cast<float *>(out) : static_cast<float *>(ctx->ws[t & 1].ptr);
-                if ((st = modepair_tc(ctx, src, t == 0, dst, P, Q, n[a0], n[a1], m[a0], m[a1], x[a0], a[a0], b[a0],
-                                      x[a1], a[a1], b[a1], prec, sm)))
-                    return st;
-                P *= (int64_t)m[a0] * m[a1];
-                src = dst;
-            }
-            return CHEB_OK;
-        }
-    }
     const size_t esz = prec == CHEB_FP64 ? sizeof(double) : sizeof(float);
     // the largest intermediate of the chain (modes d-1..s evaluated)
     size_t cap = 0;

@@ -182,19 +182,6 @@ cheb_status modeprod_tc_raw(const void *X, int x_f64, const double *B, float *ou
                             const double *xpts = nullptr, double ta = -1.0, double tb = 1.0,
                             long long wait_limit = kDefaultWaitCycles);
 
-// Two mode products fused (tc_modepair.cu): on a row-major X of shape
-// [P][n_a][n_b][Q] (FP64 when x_f64, else FP32),
-//   out[p][j_a][j_b][q] = sum T_a[j_a, k_a] T_b[j_b, k_b] X[p][k_a][k_b][q],
-// T_a, T_b formed in the kernel from the points xa (m_a on [aa, ba]) and xb
-// (m_b on [ab, bb]); FP32 out of shape [P][m_a][m_b][Q]. modepair_tc_fits
-// tells whether a shape fits the kernel's shared memory, TMEM and tile limits
-// (otherwise modepair_tc returns CHEB_EUNSUPPORTED). Launched with
-// programmatic stream serialization like modeprod_tc.
-bool modepair_tc_fits(int n_a, int n_b, int m_a, int m_b, int x_f64, int64_t Q, cheb_precision prec);
-cheb_status modepair_tc(cheb_ctx *ctx, const void *X, int x_f64, float *out, int64_t P, int64_t Q, int n_a, int n_b,
-                        int m_a, int m_b, const double *xa, double aa, double ba, const double *xb, double ab,
-                        double bb, cheb_precision prec, cudaStream_t st);
-
 // Evaluation at the Lobatto nodes E[k, l] = cos(pi l k / N), cached per n.
 cheb_status node_eval_matrix(cheb_ctx *ctx, int n, const double **out);
 

@@ -306,16 +306,16 @@ def abs_kappa(c, xs, a=None, b=None):
 
 @pytest.mark.parametrize("prec", SPLITS)
 @pytest.mark.parametrize("shape,m", [
-    ((17, 18, 34, 9), (40, 17, 33, 5)),       # K tails of 1 and 2 columns in both products; ragged tiles
-    ((33, 33, 33, 33), (130, 64, 100, 3)),    # m_a > 128 in the first pair, m_b = 3 in the second
-    ((5, 64, 64, 2), (3, 128, 1, 9)),         # m_b = 128 (four MMA 2 pieces), n_a = 64, m_a = 1
-    ((9, 2, 3, 4, 33, 17), (11, 3, 2, 5, 7, 64)),   # d = 6: three fused pairs, the middle one with P, Q > 1
+    ((17, 18, 34, 9), (40, 17, 33, 5)),       # K tails of one and two columns; ragged tiles
+    ((33, 33, 33, 33), (130, 64, 100, 3)),    # 130 points on one mode, 3 on another
+    ((5, 64, 64, 2), (3, 128, 1, 9)),         # n = 64 and n = 2, one point on a mode
+    ((9, 2, 3, 4, 33, 17), (11, 3, 2, 5, 7, 64)),   # d = 6
 ])
-def test_fused_mode_pairs(ctx, shape, m, prec):
-    """Even d with the split forms runs the mode pairs (0, 1), (2, 3), ... in fused launches
-    (both products of a pair in one CTA). Shapes that exercise the K tails, ragged tiles of
-    four units, padded rows and columns of both MMAs, and points outside the domain, against
-    the oracle within d u_form kappa (kappa from |T| on the actual points)."""
+def test_four_and_six_mode_shapes(ctx, shape, m, prec):
+    """d = 4 and d = 6 split-form chains on shapes that exercise the K tails of one and two
+    columns, ragged row tiles, padded rows and columns of the MMAs, point counts from 1 to
+    130, and points outside the domain, against the oracle within d u_form kappa (kappa from
+    |T| on the actual points)."""
     rng = np.random.default_rng(sum(shape) + sum(m))
     d = len(shape)
     c = rng.standard_normal(shape)
