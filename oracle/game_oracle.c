@@ -7,7 +7,14 @@
  * benchmark's CPU-baseline leg; never by the library.
  *
  * Model (Section 2, linear-quadratic specification, all m_i equal to m):
- *   g_i(p, u) = (1/m) sum_{j != i} k_ij (p_j - p_i) - c_i p_i + beta_i u_i,
+ *   g_i(p, u) = (1/m) sum_{j != i} k_ij (p_j - p_i) - c_i p_i + beta_i u_i
+ *               + u_i sum_{l != i} gamma_il u_l,
+ * where the last term (an emission-interaction coupling, zero in the paper's
+ * examples) makes g non-separable in the controls: Section 2.1 Step 0 then
+ * interpolates g at every state node as a function of all controls on
+ * [0, U_M]^J (the "g-interpolants"), and Steps 1-2 evaluate those
+ * interpolants at the controls (Section 3.3); with gamma = 0 the same code
+ * evaluates g directly, which the interpolant reproduces exactly.
  *   G_i(p, u_i) = u_i (A_i - u_i / 2) - (phi_i / 2) p_i^2,
  *   delta_h = 1 - rho h, next state p + h g(p, u)           (eq. ecgtimedisc),
  *   V_i(p) = max_{u_i >= 0} { h G_i + delta_h V_i(p + h g(p, [u_i, u*_{-i}])) }.
@@ -49,6 +56,7 @@ typedef struct {
     double m;          /* common region measure m_i */
     double A[4], beta[4], phi[4], c[4];
     double rho;
+    double gamma[16];  /* J x J emission-interaction coupling (diagonal unused) */
 } orc_game_params;
 
 typedef struct {
@@ -56,6 +64,7 @@ typedef struct {
     int n;             /* state nodes per player (N^p + 1) */
     int n_u;           /* control nodes (N^u + 1) */
     long max_iter;
+    int g_interp;      /* 1: Steps 1-2 evaluate g through the Step 0 interpolants */
 } orc_game_opts;
 
 static long ipow(int b, int e)
@@ -73,8 +82,56 @@ void orc_game_dynamics(const orc_game_params *P, const double *p, const double *
         double coup = 0.0;
         for (int j = 0; j < J; ++j)
             if (j != i) coup += P->K[i * J + j] * (p[j] - p[i]);
-        g[i] = coup / P->m - P->c[i] * p[i] + P->beta[i] * u[i];
+        double inter = 0.0;
+        for (int l = 0; l < J; ++l)
+            if (l != i) inter += P->gamma[i * J + l] * u[l];
+        g[i] = coup / P->m - P->c[i] * p[i] + P->beta[i] * u[i] + u[i] * inter;
     }
+}
+
+/* Step 0 (Section 2.1): the interpolants of g_l(pbar, .) at one state node in
+ * all J controls, on the tensor grid of n_u Chebyshev-Lobatto control nodes
+ * per player, u~_k = (U_M/2)(cos(pi k/N_u) + 1) on [0, U_M]. gc receives J
+ * coefficient tensors of n_u^J entries (component l first), fitted by
+ * eq. (forcoef) mode by mode. */
+void orc_game_g_interp(const orc_game_params *P, const orc_game_opts *O, const double *pbar, double *gc)
+{
+    int J = P->J, nu = O->n_u, Nu = nu - 1;
+    long NU = ipow(nu, J);
+    int nd[4];
+    for (int s = 0; s < J; ++s) nd[s] = nu;
+    double *vals = (double *)malloc(sizeof(double) * (size_t)NU * (size_t)J);
+    for (long t = 0; t < NU; ++t) {
+        double uu[4], g[4];
+        long rem = t;
+        for (int s = J - 1; s >= 0; --s) {
+            int k = (int)(rem % nu);
+            rem /= nu;
+            uu[s] = 0.5 * O->U_M * (cos(M_PI * (double)k / (double)Nu) + 1.0);
+        }
+        orc_game_dynamics(P, pbar, uu, g);
+        for (int l = 0; l < J; ++l) vals[(size_t)l * NU + t] = g[l];
+    }
+    for (int l = 0; l < J; ++l) orc_fit_nd(J, nd, vals + (size_t)l * NU, gc + (size_t)l * NU);
+    free(vals);
+}
+
+/* g(pbar, u) through the Step 0 interpolants gc (Section 3.3: the node's own
+ * interpolant evaluated at its controls). */
+void orc_game_g_eval(const orc_game_params *P, const orc_game_opts *O, const double *gc, const double *u,
+                     double *g)
+{
+    int J = P->J, nu = O->n_u;
+    long NU = ipow(nu, J);
+    int nd[4];
+    double xr[4];
+    for (int s = 0; s < J; ++s) {
+        nd[s] = nu;
+        xr[s] = 2.0 * u[s] / O->U_M - 1.0;
+    }
+    double *work = (double *)malloc(sizeof(double) * (size_t)NU);
+    for (int l = 0; l < J; ++l) g[l] = orc_eval_nested(J, nd, gc + (size_t)l * NU, xr, work);
+    free(work);
 }
 
 /* State node j (row-major multi-index, last player fastest) on [0, P_M]^J:
@@ -161,19 +218,28 @@ int orc_game_node_update(const orc_game_params *P, const orc_game_opts *O, int i
     for (int s = 0; s < J; ++s) nd[s] = O->n;
     long NP = ipow(O->n, J);
     double *work = (double *)malloc(sizeof(double) * (size_t)NP);
+    double *gc = NULL;
+    if (O->g_interp) {
+        gc = (double *)malloc(sizeof(double) * (size_t)J * (size_t)ipow(nu, J));
+        orc_game_g_interp(P, O, pbar, gc);
+    }
     double W[128], a[128];
     for (int k = 0; k <= Nu; ++k) {
         double uk = 0.5 * O->U_M * (cos(M_PI * (double)k / (double)Nu) + 1.0);
         double uu[4], g[4], xr[4];
         for (int s = 0; s < J; ++s) uu[s] = u_old[s];
         uu[i] = uk;
-        orc_game_dynamics(P, pbar, uu, g);
+        if (gc)
+            orc_game_g_eval(P, O, gc, uu, g);
+        else
+            orc_game_dynamics(P, pbar, uu, g);
         for (int s = 0; s < J; ++s) xr[s] = 2.0 * (pbar[s] + O->h * g[s]) / O->P_M - 1.0;
         double Vq = orc_eval_nested(J, nd, Vcoef_i, xr, work);
         double G = uk * (P->A[i] - 0.5 * uk) - 0.5 * P->phi[i] * pbar[i] * pbar[i];
         W[k] = O->h * G + delta * Vq;
     }
     free(work);
+    free(gc);
     orc_c1v(nu, W, a);
     double val;
     double y = argmax_series(nu, a, &val, concave);

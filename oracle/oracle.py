@@ -50,12 +50,12 @@ _ip = C.POINTER(C.c_int)
 class GameParams(C.Structure):
     _fields_ = [("J", C.c_int), ("K", C.c_double * 16), ("m", C.c_double),
                 ("A", C.c_double * 4), ("beta", C.c_double * 4), ("phi", C.c_double * 4),
-                ("c", C.c_double * 4), ("rho", C.c_double)]
+                ("c", C.c_double * 4), ("rho", C.c_double), ("gamma", C.c_double * 16)]
 
 
 class GameOpts(C.Structure):
     _fields_ = [("h", C.c_double), ("P_M", C.c_double), ("U_M", C.c_double), ("tol", C.c_double),
-                ("n", C.c_int), ("n_u", C.c_int), ("max_iter", C.c_long)]
+                ("n", C.c_int), ("n_u", C.c_int), ("max_iter", C.c_long), ("g_interp", C.c_int)]
 
 
 def _declare(L):
@@ -78,6 +78,8 @@ def _declare(L):
     L.orc_get_threads.restype = C.c_int
     L.orc_game_dynamics.argtypes = [C.POINTER(GameParams), _dp, _dp, _dp]
     L.orc_game_node.argtypes = [C.POINTER(GameOpts), C.c_int, C.c_long, _dp, _dp]
+    L.orc_game_g_interp.argtypes = [C.POINTER(GameParams), C.POINTER(GameOpts), _dp, _dp]
+    L.orc_game_g_eval.argtypes = [C.POINTER(GameParams), C.POINTER(GameOpts), _dp, _dp, _dp]
     L.orc_game_node_update.argtypes = [C.POINTER(GameParams), C.POINTER(GameOpts), C.c_int, _dp,
                                        _dp, _dp, _dp, _dp, _ip]
     L.orc_game_node_update.restype = C.c_int
@@ -240,16 +242,22 @@ def make_params(p) -> GameParams:
         g.phi[s] = float(p["phi"][s])
         g.c[s] = float(p["c"][s])
     g.rho = float(p["rho"])
+    G = np.asarray(p.get("gamma", np.zeros((J, J))), dtype=np.float64).reshape(J, J)
+    for t in range(J * J):
+        g.gamma[t] = G.flat[t]
     return g
 
 
 def make_opts(n: int, h: float = 1e-2, P_M: float = 1.0, U_M: float = 1.0, tol: float = 1e-10,
-              n_u: int | None = None, max_iter: int = 100000) -> GameOpts:
+              n_u: int | None = None, max_iter: int = 100000, g_interp: bool = False) -> GameOpts:
+    """g_interp: evaluate g in Steps 1-2 through the Step 0 interpolants in the controls
+    (the general method; required when the coupling gamma is nonzero)."""
     o = GameOpts()
     o.h, o.P_M, o.U_M, o.tol = float(h), float(P_M), float(U_M), float(tol)
     o.n = int(n)
     o.n_u = int(n if n_u is None else n_u)
     o.max_iter = int(max_iter)
+    o.g_interp = int(bool(g_interp))
     return o
 
 
@@ -269,6 +277,23 @@ def game_nodes(opts: GameOpts, J: int):
     for j in range(NP):
         lib().orc_game_node(C.byref(opts), J, j, _p(pb[j]), _p(xr[j]))
     return pb, xr
+
+
+def game_g_interp(p, opts: GameOpts, pbar) -> np.ndarray:
+    """Step 0: the J interpolants of g(pbar, .) in the controls (J x n_u^J coefficients)."""
+    P = make_params(p)
+    J = P.J
+    gc = np.empty(J * opts.n_u ** J)
+    lib().orc_game_g_interp(C.byref(P), C.byref(opts), _p(_f64(pbar)), _p(gc))
+    return gc.reshape(J, -1)
+
+
+def game_g_eval(p, opts: GameOpts, gc, u) -> np.ndarray:
+    """g at controls u through the Step 0 interpolants gc."""
+    P = make_params(p)
+    g = np.empty(P.J)
+    lib().orc_game_g_eval(C.byref(P), C.byref(opts), _p(_f64(gc)), _p(_f64(u)), _p(g))
+    return g
 
 
 def game_node_update(p, opts: GameOpts, i: int, pbar, u_old, Vcoef_i):

@@ -112,15 +112,18 @@ def neighbour_matrix(J: int, k: float = 1.0) -> np.ndarray:
     return K * k
 
 
-def game_params(J: int = 3, A=None, phi=None, beta=None, c=None, rho=None, k=None, m=None):
-    """A parameter dict with the paper's nominal values for anything not given."""
+def game_params(J: int = 3, A=None, phi=None, beta=None, c=None, rho=None, k=None, m=None, gamma=None):
+    """A parameter dict with the paper's nominal values for anything not given. gamma (J x J,
+    default zero) is the emission-interaction coupling u_i sum_{l != i} gamma_il u_l of the
+    dynamics, zero in the paper's examples."""
     def vec(v, name):
         v = NOMINAL[name] if v is None else v
         return np.broadcast_to(np.asarray(v, dtype=np.float64), (J,)).copy()
     kk = NOMINAL["k"] if k is None else float(k)
     return {"J": J, "K": neighbour_matrix(J, kk), "m": NOMINAL["m"] if m is None else float(m),
             "A": vec(A, "A"), "beta": vec(beta, "beta"), "phi": vec(phi, "phi"),
-            "c": vec(c, "c"), "rho": NOMINAL["rho"] if rho is None else float(rho)}
+            "c": vec(c, "c"), "rho": NOMINAL["rho"] if rho is None else float(rho),
+            "gamma": np.zeros((J, J)) if gamma is None else np.asarray(gamma, dtype=np.float64).reshape(J, J)}
 
 
 def draw_game_params(rng: SplitMix64, J: int = 3, spread: float = 0.3):

@@ -442,3 +442,89 @@ def test_mlp_oracle_first_adam_step_is_a_signed_step():
     O.adam_step(w, g, m, v, lr, 0.9, 0.999, eps, 1)
     assert np.abs(w - (w0 - lr * g / (np.abs(g) + eps))).max() < 1e-15
     assert np.abs(m - 0.1 * g).max() < 1e-15 and np.abs(v - 0.001 * g * g).max() < 1e-15
+
+
+# ---- non-separable dynamics: Step 0 g-interpolants (Section 2.1, Section 3.3) --------
+
+def _coupling(J, scale=0.4, seed=7):
+    rng = np.random.default_rng(seed)
+    G = rng.uniform(-scale, scale, (J, J))
+    np.fill_diagonal(G, 0.0)
+    return G
+
+
+@pytest.mark.parametrize("J,n_u", [(2, 2), (3, 3), (3, 6), (4, 2)])
+def test_g_interpolants_reproduce_the_dynamics(J, n_u):
+    """The dynamics are affine in each control separately (bilinear in pairs of controls), so
+    their interpolant on n_u >= 2 Lobatto control nodes per player reproduces them exactly at
+    any control, also off the nodes; with the coupling, g_i moves with the other players'
+    controls (it is not separable)."""
+    p = I.game_params(J, gamma=_coupling(J))
+    opts = O.make_opts(5, n_u=n_u, U_M=1.0, g_interp=True)
+    rng = np.random.default_rng(J * 10 + n_u)
+    for _ in range(4):
+        pb = rng.uniform(0, 1, J)
+        gc = O.game_g_interp(p, opts, pb)
+        for _ in range(6):
+            u = rng.uniform(0, 1, J)
+            assert np.allclose(O.game_g_eval(p, opts, gc, u), O.game_dynamics(p, pb, u), rtol=0, atol=1e-14)
+    pb, u = rng.uniform(0, 1, J), rng.uniform(0, 1, J)
+    u2 = u.copy()
+    u2[1] += 0.3
+    assert abs(O.game_dynamics(p, pb, u2)[0] - O.game_dynamics(p, pb, u)[0]) > 1e-3
+
+
+@pytest.mark.parametrize("J", [2, 3])
+def test_g_interpolant_path_without_coupling_is_the_lq_iteration(J):
+    """With gamma = 0 the Steps 1-2 through the Step 0 interpolants give the same iterates as
+    the direct evaluation of g (and so the same as the closed-form LQ recursion pinned above)."""
+    p = I.game_params(J)
+    a = O.game_solve(p, O.make_opts(5, tol=0.0, max_iter=4, P_M=0.25))
+    b = O.game_solve(p, O.make_opts(5, tol=0.0, max_iter=4, P_M=0.25, g_interp=True))
+    assert np.abs(a["Vcoef"] - b["Vcoef"]).max() <= 1e-13 * np.abs(a["Vcoef"]).max()
+    assert np.abs(a["u"] - b["u"]).max() <= 1e-13
+
+
+@pytest.mark.parametrize("J", [2, 3])
+def test_coupled_node_update_matches_direct_maximisation(J):
+    """With the coupling every next-state coordinate moves with the player's own control, so
+    W(u) = h G_i + delta V_i(pbar + h g(pbar, [u, u_-i])) is a polynomial of degree at most
+    J (n - 1) + 2 in u; with that many control nodes the C1v interpolant of Step 2 is exact and
+    the node update must equal a brute-force maximisation of W on a fine grid."""
+    n = 4
+    n_u = J * (n - 1) + 3
+    p = I.game_params(J, gamma=_coupling(J, 0.5))
+    opts = O.make_opts(n, n_u=n_u, tol=0.0, max_iter=8, g_interp=True)
+    res = O.game_solve(p, opts)
+    pb, _ = O.game_nodes(opts, J)
+    delta = 1 - p["rho"] * 1e-2
+    ug = np.linspace(0, 1, 1001)
+    for j in (0, 5, n ** J - 1):
+        for i in range(J):
+            uo = res["u"][:, j]
+            us, vs, inside, conc = O.game_node_update(p, opts, i, pb[j], uo, res["Vcoef"][i])
+            vals = []
+            for u in ug:
+                uu = uo.copy()
+                uu[i] = u
+                q = pb[j] + 1e-2 * O.game_dynamics(p, pb[j], uu)
+                Vq = O.eval_direct(res["Vcoef"][i].reshape((n,) * J), 2 * q - 1)
+                vals.append(1e-2 * (u * (p["A"][i] - u / 2) - p["phi"][i] / 2 * pb[j][i] ** 2) + delta * Vq)
+            vals = np.array(vals)
+            assert vs >= vals.max() - 1e-14
+            assert abs(vs - vals.max()) < 2e-9      # grid step 1e-3
+            assert abs(us - ug[int(np.argmax(vals))]) < 2e-3
+
+
+def test_coupled_symmetric_players_coincide():
+    """Players 1 and 3 of the 3-player chain with identical parameters and a coupling that is
+    symmetric under the swap of players 1 and 3 stay symmetric iterate by iterate."""
+    G = np.array([[0.0, 0.3, -0.2], [0.1, 0.0, 0.1], [-0.2, 0.3, 0.0]])
+    p = I.game_params(3, gamma=G)
+    n = 4
+    res = O.game_solve(p, O.make_opts(n, n_u=8, tol=0.0, max_iter=5, g_interp=True))
+    V, u = res["Vnod"].reshape((3, n, n, n)), res["u"].reshape((3, n, n, n))
+    assert np.abs(V[0] - np.transpose(V[2], (2, 1, 0))).max() <= 1e-12 * np.abs(V).max()
+    assert np.abs(u[0] - np.transpose(u[2], (2, 1, 0))).max() <= 1e-12
+    base = O.game_solve(I.game_params(3), O.make_opts(n, n_u=8, tol=0.0, max_iter=5))
+    assert np.abs(base["Vnod"] - res["Vnod"]).max() > 1e-6      # the coupling changes the game
