@@ -293,12 +293,21 @@ CHEB_API cheb_status cheb_eval_grid_noalloc_status(void *stream);
 /* ------------------------------------------------------------------------
  * The J-player pollution game (Section 2, linear-quadratic specification,
  * time step h, Section 2.1):
- *   g_i(p, u) = (1/m) sum_{j != i} K[i][j] (p_j - p_i) - c_i p_i + beta_i u_i,
+ *   g_i(p, u) = (1/m) sum_{j != i} K[i][j] (p_j - p_i) - c_i p_i + beta_i u_i
+ *               + u_i sum_{l != i} gamma[i][l] u_l,
  *   G_i(p, u_i) = u_i (A_i - u_i/2) - (phi_i/2) p_i^2,   delta_h = 1 - rho h,
  *   V_i(p) = max_{0 <= u_i <= U_M} h G_i + delta_h V_i(p + h g(p, [u_i, u*_{-i}])).
  * The printed coupling term k_ij (p_i - p_j) is anti-diffusive with k_ij >= 0;
  * the paper's matrices have zero row sums, and the term is taken as
  * K[i][j] (p_j - p_i), i.e. (K p)_i / m. Only the off-diagonal of K is used.
+ * The coupling gamma (an emission-interaction term, zero in the paper's
+ * examples) makes g non-separable in the controls: then the general method of
+ * Section 2.1 runs - Step 0 interpolates g at every state node in all J
+ * controls on n_u Lobatto control nodes per player (the g-interpolants),
+ * Steps 1-2 evaluate them along each player's control line (per node, by
+ * contraction with the other players' Chebyshev rows, Section 3.3) and
+ * evaluate V_i at the resulting next states for the n_u control nodes, and
+ * Step 3 maximises the C1v interpolant of those values in the control.
  * ------------------------------------------------------------------------ */
 typedef struct {
     int32_t J;          /* players, 1 <= J <= 4 */
@@ -309,6 +318,8 @@ typedef struct {
     double phi[4];      /* damage cost phi_i >= 0 */
     double c[4];        /* natural decay c_i */
     double rho;         /* discount rate, 0 < rho h < 1 */
+    double gamma[16];   /* J x J row-major coupling, diagonal ignored; all zero for the
+                           paper's linear-quadratic game */
 } cheb_game_params;
 
 typedef struct {
@@ -317,15 +328,22 @@ typedef struct {
     double U_M;         /* control interval [0, U_M] */
     double tol;         /* stop when max_{i,j} |V^[r+1]_i - V^[r]_i| < tol at the nodes */
     int32_t n;          /* state nodes per player N^p + 1, 3 <= n <= 33 */
-    int32_t n_u;        /* control nodes N^u + 1; 0 means n. Must be 0 or >= n:
-                           then the control interpolant of Step 2 is exact and the
-                           maximisation runs on the exact one-variable polynomial */
+    int32_t n_u;        /* control nodes N^u + 1; 0 means n. Without coupling it must
+                           be 0 or >= n: then the control interpolant of Step 2 is exact
+                           and the maximisation runs on the exact one-variable
+                           polynomial. With coupling (or g_interp) 2 <= n_u <= 33: the
+                           g-interpolants and the interpolant of Step 2 use n_u nodes */
     int64_t max_iter;   /* iteration cap (CHEB_ENOCONV when reached) */
     int32_t prec;       /* cheb_precision of the evaluation products */
     int32_t polish_fp64;/* split forms: once the split iteration stagnates, 1 =
                            continue with FP64-level accuracy in double-float
                            (the CHEB_DF64 update), 2 = continue on the FP64 pipe
                            (the CHEB_FP64 update); 0 = stop there (CHEB_ESTALL) */
+    int32_t g_interp;   /* 1: run the general method (g-interpolants, Step 2 on the
+                           control nodes) also without coupling; implied by a nonzero
+                           gamma. The general method runs in CHEB_FP64 only
+                           (CHEB_EUNSUPPORTED for the other forms) and needs
+                           n^J J n_u^J doubles of workspace per instance */
 } cheb_game_opts;
 
 typedef struct {

@@ -240,18 +240,25 @@ def game_params(p) -> GameParams:
         g.phi[s] = float(p["phi"][s])
         g.c[s] = float(p["c"][s])
     g.rho = float(p["rho"])
+    G = np.asarray(p.get("gamma", np.zeros((J, J))), dtype=np.float64).reshape(J, J)
+    for t in range(J * J):
+        g.gamma[t] = float(G.flat[t])
     return g
 
 
 def game_opts(n: int, h: float = 1e-2, P_M: float = 1.0, U_M: float = 1.0, tol: float = 1e-10,
-              max_iter: int = 100000, prec="fp64", polish_fp64=True, n_u: int = 0) -> GameOpts:
+              max_iter: int = 100000, prec="fp64", polish_fp64=True, n_u: int = 0,
+              g_interp: bool = False) -> GameOpts:
     """polish_fp64 (split forms, once the split iteration stagnates): True or 1 continue in
-    double-float (FP64-level accuracy on the FP32 pipe), 2 on the FP64 pipe, False stop."""
+    double-float (FP64-level accuracy on the FP32 pipe), 2 on the FP64 pipe, False stop.
+    g_interp: the general method (g-interpolants in the controls, Step 2 on n_u control
+    nodes), implied by a nonzero coupling gamma in the parameters."""
     o = GameOpts()
     o.h, o.P_M, o.U_M, o.tol = float(h), float(P_M), float(U_M), float(tol)
     o.n, o.n_u, o.max_iter = int(n), int(n_u), int(max_iter)
     o.prec = precision(prec)
     o.polish_fp64 = 2 if polish_fp64 == 2 else int(bool(polish_fp64))
+    o.g_interp = int(bool(g_interp))
     return o
 
 

@@ -32,13 +32,13 @@ class ChebError(RuntimeError):
 class GameParams(C.Structure):
     _fields_ = [("J", C.c_int32), ("K", C.c_double * 16), ("m", C.c_double),
                 ("A", C.c_double * 4), ("beta", C.c_double * 4), ("phi", C.c_double * 4),
-                ("c", C.c_double * 4), ("rho", C.c_double)]
+                ("c", C.c_double * 4), ("rho", C.c_double), ("gamma", C.c_double * 16)]
 
 
 class GameOpts(C.Structure):
     _fields_ = [("h", C.c_double), ("P_M", C.c_double), ("U_M", C.c_double), ("tol", C.c_double),
                 ("n", C.c_int32), ("n_u", C.c_int32), ("max_iter", C.c_int64), ("prec", C.c_int32),
-                ("polish_fp64", C.c_int32)]
+                ("polish_fp64", C.c_int32), ("g_interp", C.c_int32)]
 
 
 class GameResult(C.Structure):

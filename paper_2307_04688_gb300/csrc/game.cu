@@ -274,9 +274,9 @@ static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const
     return CHEB_OK;
 }
 
-cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std::vector<int> &members,
-                        const cheb_game_params *params, const cheb_game_opts *opts, cheb_game_result *res,
-                        cudaStream_t st)
+cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int general, int n_u,
+                        const std::vector<int> &members, const cheb_game_params *params,
+                        const cheb_game_opts *opts, cheb_game_result *res, cudaStream_t st)
 {
     const int B = (int)members.size();
     const size_t per = (size_t)J * NP;       // doubles per instance per array
@@ -287,7 +287,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     size_t bytes = 0;
     auto rnd = [](size_t x) { return (x + 255) & ~size_t(255); };
     const bool any_df = prec == CHEB_DF64 || (prec != CHEB_FP64 && opts[members[0]].polish_fp64 == 1);
-    bytes += 9 * rnd(arr) + (any_df ? rnd(arr) : 0) + rnd(sizeof(double) * 64) + rnd(sizeof(GameDev) * B) +
+    bytes += 9 * rnd(arr) + (any_df ? rnd(arr) : 0) + rnd(sizeof(double) * 128) + rnd(sizeof(GameDev) * B) +
              rnd(sizeof(GameStat) * B) + rnd(tc_bytes);
     cheb_status r = ctx->game.reserve(bytes);
     if (r) return r;
@@ -307,17 +307,37 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     double *fit0 = reinterpret_cast<double *>(take(arr));
     double *fit1 = reinterpret_cast<double *>(take(arr));
     double *init = reinterpret_cast<double *>(take(arr));
-    double *nodes = reinterpret_cast<double *>(take(sizeof(double) * 64));
+    double *nodes = reinterpret_cast<double *>(take(sizeof(double) * 128));
     GameDev *d_inst = reinterpret_cast<GameDev *>(take(sizeof(GameDev) * B));
     GameStat *d_stat = reinterpret_cast<GameStat *>(take(sizeof(GameStat) * B));
     uint8_t *tc_ws = take(tc_bytes);
     float *Cdf_all = any_df ? reinterpret_cast<float *>(take(arr)) : nullptr;   // (hi, lo) per coefficient
     (void)init;
 
-    // nodes cos(pi k / N) (the integer argument is exact)
-    std::vector<double> hn(n);
+    // nodes cos(pi k / N) (the integer argument is exact); for the general
+    // method the control nodes follow them in the same buffer
+    std::vector<double> hn(n + (general ? n_u : 0));
     for (int k = 0; k < n; ++k) hn[k] = std::cos(M_PI * (double)k / (double)(n - 1));
-    CHEB_CUDA_TRY(cudaMemcpyAsync(nodes, hn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    for (int k = 0; general && k < n_u; ++k) hn[n + k] = std::cos(M_PI * (double)k / (double)(n_u - 1));
+    CHEB_CUDA_TRY(cudaMemcpyAsync(nodes, hn.data(), sizeof(double) * hn.size(), cudaMemcpyHostToDevice, st));
+    // general method: the g-interpolants and two workspaces for their fit
+    double *Gc_all = nullptr, *gtmp0 = nullptr, *gtmp1 = nullptr;
+    const double *Mu = nullptr;
+    size_t gc_per = 0;
+    if (general) {
+        int64_t NU = 1;
+        for (int s = 0; s < J; ++s) NU *= n_u;
+        gc_per = (size_t)NP * J * NU;
+        const size_t gbytes = sizeof(double) * gc_per * B;
+        if ((double)gbytes * 3.0 > 48e9)
+            return fail(CHEB_EUNSUPPORTED, "game_solve: the g-interpolants of this batch need more than 48 GB");
+        if ((r = ctx->game_aux.reserve(3 * ((gbytes + 255) & ~size_t(255))))) return r;
+        uint8_t *gb = static_cast<uint8_t *>(ctx->game_aux.ptr);
+        Gc_all = reinterpret_cast<double *>(gb);
+        gtmp0 = reinterpret_cast<double *>(gb + ((gbytes + 255) & ~size_t(255)));
+        gtmp1 = reinterpret_cast<double *>(gb + 2 * ((gbytes + 255) & ~size_t(255)));
+        if ((r = dct_matrix(ctx, n_u, &Mu))) return r;
+    }
 
     std::vector<GameDev> hinst(B);
     std::vector<GameStat> hstat(B);
@@ -362,6 +382,12 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         g.Vn_new = Vn_new_all + per * q;
         g.X = X_all + per * q;
         g.nodes = nodes;
+        g.general = general;
+        g.n_u = general ? n_u : 0;
+        for (int t = 0; t < J * J; ++t) g.gamma[t] = (t % (J + 1) == 0) ? 0.0 : p.gamma[t];
+        g.Gc = general ? Gc_all + gc_per * q : nullptr;
+        g.Mu = Mu;
+        g.unodes = general ? nodes + n : nullptr;
         g.V0 = res[b].V0;
         g.u0 = res[b].u0;
         any_v0 |= res[b].V0 != nullptr;
@@ -386,6 +412,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
     CHEB_CUDA_TRY(cudaGetLastError());
     const bool df_refit = prec != CHEB_FP64 && prec != CHEB_DF64;
     if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, nullptr, df_refit, st))) return r;
+    if (general && (r = game_general_prepare(ctx, d_inst, B, J, NP, n_u, Gc_all, gtmp0, gtmp1, st))) return r;
 
     // ---- one iteration ----
     const unsigned node_blocks = (unsigned)((NP + 127) / 128);
@@ -395,7 +422,10 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
             restart_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);
             CHEB_CUDA_TRY(cudaGetLastError());
         }
-        {
+        if (general) {
+            // Steps 1-3 of the general method (FP64), then the common refit and commit
+            if ((e = game_general_player(d_inst, d_stat, B, J, NP, s))) return e;
+        } else {
             ProfScope prof("game_next_state", s);
             next_state_kernel<<<dim3(node_blocks, B), 128, 0, s>>>(d_inst, d_stat);
         }
@@ -407,7 +437,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std
         if (prec == CHEB_DF64 || (split && hinst[0].polish && hinst[0].polish_mode == 2)) {
             if ((e = game_df_player(d_inst, d_stat, B, J, NP, s))) return e;
         }
-        if (prec == CHEB_FP64 || (split && hinst[0].polish && hinst[0].polish_mode == 0)) {
+        if (!general && (prec == CHEB_FP64 || (split && hinst[0].polish && hinst[0].polish_mode == 0))) {
             ProfScope prof("game_player_f64", s);
             player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
         }
@@ -548,7 +578,7 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
     CHEB_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     struct Key {
-        int J, n, prec;
+        int J, n, prec, general, n_u;
         std::vector<int> members;
     };
     std::vector<Key> groups;
@@ -557,8 +587,23 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
         const cheb_game_opts &o = opts[b];
         if (p.J < 1 || p.J > 4) return fail(CHEB_EINVAL, "game_solve: J must be in [1, 4]");
         if (o.n < 3 || o.n > kGameNMax) return fail(CHEB_EINVAL, "game_solve: n must be in [3, 33]");
-        if (o.n_u != 0 && o.n_u < o.n)
+        bool coupled = false;
+        for (int x = 0; x < p.J; ++x)
+            for (int y = 0; y < p.J; ++y)
+                if (x != y && p.gamma[x * p.J + y] != 0.0) coupled = true;
+        for (int t = 0; t < p.J * p.J; ++t)
+            if (!std::isfinite(p.gamma[t])) return fail(CHEB_EINVAL, "game_solve: gamma not finite");
+        if (o.g_interp < 0 || o.g_interp > 1) return fail(CHEB_EINVAL, "game_solve: g_interp must be 0 or 1");
+        const int general = (coupled || o.g_interp) ? 1 : 0;
+        const int n_u = general ? (o.n_u == 0 ? o.n : o.n_u) : 0;
+        if (general) {
+            if (n_u < 2 || n_u > kGameNMax)
+                return fail(CHEB_EINVAL, "game_solve: the general method needs 2 <= n_u <= 33");
+            if (o.prec != CHEB_FP64)
+                return fail(CHEB_EUNSUPPORTED, "game_solve: coupled dynamics (the general method) run in CHEB_FP64 only");
+        } else if (o.n_u != 0 && o.n_u < o.n) {
             return fail(CHEB_EUNSUPPORTED, "game_solve: n_u must be 0 or >= n (exact control interpolant)");
+        }
         if (!(o.h > 0) || !(p.rho > 0) || !(p.rho * o.h < 1) || !(o.P_M > 0) || !(o.U_M > 0) || !(p.m > 0) ||
             !(o.tol >= 0) || o.max_iter < 1)
             return fail(CHEB_EINVAL,
@@ -581,17 +626,17 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
         res[b].iters_split = 0;
         bool found = false;
         for (auto &g : groups)
-            if (g.J == p.J && g.n == o.n && g.prec == o.prec) {
+            if (g.J == p.J && g.n == o.n && g.prec == o.prec && g.general == general && g.n_u == n_u) {
                 g.members.push_back(b);
                 found = true;
                 break;
             }
-        if (!found) groups.push_back({p.J, o.n, o.prec, {b}});
+        if (!found) groups.push_back({p.J, o.n, o.prec, general, n_u, {b}});
     }
     for (auto &g : groups) {
         int NP = 1;
         for (int t = 0; t < g.J; ++t) NP *= g.n;
-        cheb_status r = solve_group(ctx, g.J, g.n, NP, g.prec, g.members, params, opts, res, st);
+        cheb_status r = solve_group(ctx, g.J, g.n, NP, g.prec, g.general, g.n_u, g.members, params, opts, res, st);
         if (r) return r;
     }
     cheb_status first = CHEB_OK;

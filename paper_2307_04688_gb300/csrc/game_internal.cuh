@@ -33,6 +33,12 @@ struct GameDev {
     // double-float path (game_df.cu)
     float *Cdf;                   // J x NP coefficient pairs (hi, lo)
     int polish_mode;              // mode a stalled split iteration continues in (0 FP64, 2 double-float)
+    // general method (game_general.cu): dynamics coupled through gamma
+    int general, n_u;             // general method on; control nodes per player
+    double gamma[16];             // J x J emission-interaction coupling
+    double *Gc;                   // NP x J x n_u^J coefficients of the g-interpolants
+    const double *Mu;             // n_u x n_u DCT-I matrix of the control interpolant
+    const double *unodes;         // cos(pi k / (n_u - 1)), k < n_u
 };
 
 // One instance's progress, written by the commit kernel.
@@ -145,9 +151,16 @@ __device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, in
     atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
 }
 
-cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, const std::vector<int> &members,
-                        const cheb_game_params *params, const cheb_game_opts *opts, cheb_game_result *res,
-                        cudaStream_t st);
+cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int general, int n_u,
+                        const std::vector<int> &members, const cheb_game_params *params,
+                        const cheb_game_opts *opts, cheb_game_result *res, cudaStream_t st);
+
+// ---- general method (game_general.cu): Step 0 g-interpolants of every instance
+// into Gc (tmp0, tmp1: workspaces of the same size, B NP J n_u^J doubles), and the
+// Steps 1-3 update of every player at every node (instances in FP64 mode) ----
+cheb_status game_general_prepare(cheb_ctx *ctx, const GameDev *d_inst, int B, int J, int NP, int n_u, double *Gc,
+                                 double *tmp0, double *tmp1, cudaStream_t st);
+cheb_status game_general_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st);
 
 // ---- double-float player update (game_df.cu): coefficient split + update ----
 cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st);

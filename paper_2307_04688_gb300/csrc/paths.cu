@@ -35,6 +35,7 @@ struct PathParams {
     int J, n;
     int64_t len1;             // n^{J-1}
     double Kmat[16], minv, c[4], beta[4];
+    double gamma[16];         // emission-interaction coupling (J x J)
     double h, P_M, U_M;
 };
 
@@ -107,7 +108,10 @@ __global__ void __launch_bounds__(kThreads) game_paths_kernel(const PathParams P
                     double coup = 0.0;
                     for (int b = 0; b < J; ++b)
                         if (b != a) coup += P.Kmat[a * J + b] * (ps[b] - ps[a]);
-                    g[a] = coup * P.minv - P.c[a] * ps[a] + P.beta[a] * us[a];
+                    double inter = 0.0;
+                    for (int b = 0; b < J; ++b)
+                        if (b != a) inter += P.gamma[a * J + b] * us[b];
+                    g[a] = coup * P.minv - P.c[a] * ps[a] + P.beta[a] * us[a] + us[a] * inter;
                 }
                 for (int a = 0; a < J; ++a) {
                     if (P.u_path) P.u_path[(k * T + t) * J + a] = us[a];
@@ -166,7 +170,10 @@ extern "C" CHEB_API cheb_status game_paths(cheb_ctx *ctx, const cheb_game_params
     P.J = J;
     P.n = n;
     P.len1 = len1;
-    for (int t = 0; t < J * J; ++t) P.Kmat[t] = params->K[t];
+    for (int t = 0; t < J * J; ++t) {
+        P.Kmat[t] = params->K[t];
+        P.gamma[t] = params->gamma[t];
+    }
     P.minv = 1.0 / params->m;
     for (int t = 0; t < J; ++t) {
         P.c[t] = params->c[t];
