@@ -223,7 +223,9 @@ CHEB_API cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, cons
  *  out     host, prod(m) values, row-major in (j_1..j_d): doubles for
  *          CHEB_FP64, floats for the split forms
  * Page-locked (pinned) host memory gives asynchronous copies at the link's
- * rate; pageable memory works but is staged by the CUDA driver. The device
+ * rate; pageable memory works but is staged by the CUDA driver. A page-locked
+ * `out` that the device can address is written directly by the last mode
+ * product (no device copy of the result, no separate copy). The device
  * copies live in context-owned buffers that grow on demand (CHEB_ENOMEM if
  * that allocation fails). Errors of the arguments are reported before any
  * copy; a CUDA error of a copy or of the evaluation returns CHEB_ECUDA.

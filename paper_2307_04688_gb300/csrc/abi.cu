@@ -522,11 +522,23 @@ cheb_status cheb_eval_grid_host(cheb_ctx *ctx, int d, const int32_t *n, const do
     CHEB_CUDA_TRY(cudaMemcpyAsync(din + xoff, ctx->pts_host, xbytes, cudaMemcpyHostToDevice, sm));
     CHEB_CUDA_TRY(cudaEventRecord(ctx->pts_done, sm));
     CHEB_CUDA_TRY(cudaMemcpyAsync(din, coeffs, cbytes, cudaMemcpyHostToDevice, sm));
-    if ((st = cheb_eval_grid(ctx, d, n, reinterpret_cast<const double *>(din), a, b, m, xd.data(), ctx->io_out.ptr,
-                             prec, stream)))
+    // a page-locked, device-mapped `out` is written by the last mode product itself
+    // (GPU stores over the host link, overlapped with the computation); any other
+    // host memory gets a device result and a copy
+    void *direct = nullptr;
+    {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer != nullptr)
+            direct = pa.devicePointer;
+        else
+            cudaGetLastError();
+    }
+    if ((st = cheb_eval_grid(ctx, d, n, reinterpret_cast<const double *>(din), a, b, m, xd.data(),
+                             direct ? direct : ctx->io_out.ptr, prec, stream)))
         return st;
     tl_ctx = ctx;
-    CHEB_CUDA_TRY(cudaMemcpyAsync(out, ctx->io_out.ptr, obytes, cudaMemcpyDeviceToHost, sm));
+    if (!direct) CHEB_CUDA_TRY(cudaMemcpyAsync(out, ctx->io_out.ptr, obytes, cudaMemcpyDeviceToHost, sm));
     CHEB_CUDA_TRY(cudaStreamSynchronize(sm));
     return CHEB_OK;
 }
