@@ -610,9 +610,9 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
                         "game_solve: need h, rho, P_M, U_M, m > 0, rho h < 1, tol >= 0, max_iter >= 1");
         if (o.prec < CHEB_FP64 || o.prec > CHEB_DF64) return fail(CHEB_EINVAL, "game_solve: bad precision");
         if (o.polish_fp64 < 0 || o.polish_fp64 > 2) return fail(CHEB_EINVAL, "game_solve: polish_fp64 must be 0, 1 or 2");
-        if (o.prec != CHEB_FP64 && o.prec != CHEB_DF64 &&
-            (p.J != 3 || (o.n != 5 && o.n != 9 && o.n != 17 && o.n != 33)))
-            return fail(CHEB_EUNSUPPORTED, "game_solve: the split forms need J = 3 and n in {5, 9, 17, 33}");
+        if (o.prec != CHEB_FP64 && o.prec != CHEB_DF64 && !tc_shape_supported(p.J, o.n))
+            return fail(CHEB_EUNSUPPORTED,
+                        "game_solve: the split forms need J in {2, 3} with n in {5, 9, 17, 33}, or J = 4 with n in {5, 9}");
         for (int t = 0; t < p.J * p.J; ++t)
             if (!std::isfinite(p.K[t])) return fail(CHEB_EINVAL, "game_solve: K not finite");
         for (int t = 0; t < p.J; ++t)

@@ -173,6 +173,7 @@ cheb_status game_refit_df(const double *V, const double *M, double *C, double *t
                           int n, int NP, const GameStat *stats, cudaStream_t st);
 
 // ---- split-precision player update (game_tc.cu) ----
+bool tc_shape_supported(int J, int n);    // (J, n) with a split player update
 size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec);
 void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws);
 cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, const GameDev *hinst, int B,

@@ -1,12 +1,16 @@
 // Split-precision player update of the game iteration on the tcgen05 tensor
-// cores (Section 3.4, Steps 1-3), J = 3 players.
+// cores (Section 3.4, Steps 1-3), J = 2, 3 or 4 players.
 //
-// For player i with other modes a < b, node j and the next-state reference
-// coordinates x(j), V_i^[r] along the next states is the series
-//     w_j[k_i] = sum_{k_a, k_b} C_i[k_i, k_a, k_b] T_{k_a}(x_a(j)) T_{k_b}(x_b(j)),
-// a dense contraction: Y[j, (k_i, k_b)] = sum_{k_a} T_{k_a}(x_a(j)) C_i[k_i, k_a, k_b]
-// is a GEMM (M = nodes, K = n, N = n * n) and w_j[k_i] = sum_{k_b} Y[j, (k_i, k_b)] T_{k_b}(x_b(j))
-// is a row-wise reduction. One fused kernel does both for a 128-node tile:
+// For player i, its first other mode a, the remaining other modes ("rest"),
+// node j and the next-state reference coordinates x(j), V_i^[r] along the next
+// states is the series
+//     w_j[k_i] = sum_{k_a, rest} C_i[k_i, k_a, rest] T_{k_a}(x_a(j)) prod_rest T(x(j)),
+// a dense contraction: Y[j, (k_i, rest)] = sum_{k_a} T_{k_a}(x_a(j)) C_i[k_i, k_a, rest]
+// is a GEMM (M = nodes, K = n, N = n^(J-1)) and w_j[k_i] is the row-wise
+// reduction of Y over the rest modes with their Chebyshev rows (J = 2: no rest,
+// w is the GEMM itself; J = 3: one mode b; J = 4: modes b, c with the products
+// T_{k_b} T_{k_c} as weights). One fused kernel does both for a 128-node tile
+// (described below for J = 3; the others differ only in the reduction):
 //  - the A operand T_{k_a}(x_a(j)) is formed in the kernel (double-float
 //    three-term recurrence, rounded to FP32, split into BF16/TF32 parts);
 //  - the B operand (C_i, columns (k_i, k_b) with k_b padded to a multiple of
@@ -67,24 +71,29 @@ template <> struct GForm<CHEB_TF32X3> {
 // The column chunk (k_i values per chunk, CH) is the tuned tile shape: it sets
 // the MMA N (CH x NBP <= 256), the shared memory of the two B stages and the
 // TMEM columns, hence how many CTAs fit on an SM.
-template <int FORM, int NN, int CH> struct Shape {
+template <int FORM, int JJ, int NN, int CH> struct Shape {
     using F = GForm<FORM>;
-    // n = 16 q + 1 (the Lobatto sizes 17, 33): the tensor cores take k_a, k_b
-    // < n - 1 with no padding, plus the k_b = n - 1 column of C_i as a group
-    // of TCOL extra B columns at the front of each chunk (column k_l holds
-    // C[k_i, k_a, n-1]); the k_a = n - 1 row is one FP32 dot product per
-    // (node, k_i) in the epilogue
-    static constexpr int TAIL = (NN > 16 && (NN - 1) % 16 == 0) ? 1 : 0;
-    static constexpr int NM = NN - TAIL;                              // k_a, k_b on the tensor cores
-    static constexpr int NBP = (NM + 15) / 16 * 16;                 // k_b padded
+    // J = 3 and n = 16 q + 1 (the Lobatto sizes 17, 33): the tensor cores take
+    // k_a, k_b < n - 1 with no padding, plus the k_b = n - 1 column of C_i as
+    // a group of TCOL extra B columns at the front of each chunk (column k_l
+    // holds C[k_i, k_a, n-1]); the k_a = n - 1 row is one FP32 dot product per
+    // (node, k_i) in the epilogue. Other J pad k_a to the instruction K.
+    static constexpr int TAIL = (JJ == 3 && NN > 16 && (NN - 1) % 16 == 0) ? 1 : 0;
+    static constexpr int NM = NN - TAIL;                              // k_a (and k_b, J = 3) on the tensor cores
+    static constexpr int NPOW = JJ == 2 ? NN * NN : JJ == 3 ? NN * NN * NN : NN * NN * NN * NN;   // n^J
+    // rest columns per k_i: J = 2 none (the k_i are the columns), J = 3 the k_b
+    // (padded), J = 4 the (k_b, k_c) pairs (padded)
+    static constexpr int RESTN = JJ == 2 ? 1 : JJ == 3 ? NM : NN * NN;
+    static constexpr int NBP = JJ == 2 ? 1 : (RESTN + 15) / 16 * 16;
     static constexpr int KP = (NM + F::KALIGN - 1) / F::KALIGN * F::KALIGN;   // k_a padded
     static constexpr int E = 16 / F::EB;                            // K elements per 16 bytes
     static constexpr int KC = KP / E;                               // 16-byte chunks along K
     static constexpr int CHKI = CH;                                 // k_i per column chunk
     static constexpr int TCOL = TAIL ? 16 : 0;                      // tail columns per chunk
-    static_assert(CH >= 1 && CH <= NN && CH * NBP + TCOL <= 256 && CH <= 16, "column chunk out of range");
     static constexpr int NCH = (NN + CHKI - 1) / CHKI;              // column chunks
-    static constexpr int NC = TCOL + CHKI * NBP;                    // columns of a stored chunk
+    static constexpr int NC = JJ == 2 ? (CHKI + 15) / 16 * 16 : TCOL + CHKI * NBP;   // columns of a stored chunk
+    static_assert(CH >= 1 && CH <= NN && NC <= 256 && (JJ == 2 || CH <= 16), "column chunk out of range");
+    static_assert(NC % 16 == 0 && (JJ == 2 || NBP % 16 == 0), "MMA N must be a multiple of 16");
     static constexpr int SPLIT_BYTES = NC * KP * F::EB;             // one split part of a chunk
     static constexpr int CHUNK_BYTES = F::SB * SPLIT_BYTES;
     static constexpr int A_SPLIT = kTile * KP * F::EB;
@@ -96,25 +105,28 @@ template <int FORM, int NN, int CH> struct Shape {
     static constexpr int TAIL_FLOATS = TAIL ? NN * CAP : 0;
     static constexpr size_t PLAYER_BYTES =     // a multiple of 128: every chunk starts 16-byte aligned
         ((size_t)NCH * CHUNK_BYTES + (size_t)TAIL_FLOATS * sizeof(float) + 127) / 128 * 128;
-    // rows staged by the prologue for the epilogue: T_{k_b} (k_b < NM), and
-    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
-    static constexpr int STG = NM + 2 * TAIL;
+    // rows staged by the prologue for the epilogue: J = 3 T_{k_b} (k_b < NM),
+    // and T_{n-1}(x_a), T_{n-1}(x_b) (TAIL); J = 4 T_{k_b} and T_{k_c}
+    static constexpr int STG = JJ == 2 ? 0 : JJ == 3 ? NM + 2 * TAIL : 2 * NN;
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) +              // w
                                    (size_t)TAIL_FLOATS * sizeof(float) +
                                    (size_t)STG * kTile * sizeof(float) + 128;
-    // CTAs per SM that shared memory allows, at most 2: the register budget
-    // the kernel is compiled to (128 per thread at 2)
-    static constexpr int MINB = 2 * (SMEM + 1024) <= 228 * 1024 ? 2 : 1;
+    // CTAs per SM that shared memory and TMEM allow, at most 2: the register
+    // budget the kernel is compiled to (128 per thread at 2)
+    static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * TMEM_ALLOC <= 512) ? 2 : 1;
 };
 
-// Column chunks the tuner tries for each node count; the first is the default
-// (the widest chunk: fewest MMA rounds, one CTA per SM).
-template <int NN> struct Chunks;
-template <> struct Chunks<5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };
-template <> struct Chunks<9> { static constexpr int count = 2, v0 = 9, v1 = 3, v2 = 3; };
-template <> struct Chunks<17> { static constexpr int count = 3, v0 = 9, v1 = 6, v2 = 3; };    // N = 160, 112, 64
-template <> struct Chunks<33> { static constexpr int count = 3, v0 = 7, v1 = 5, v2 = 3; };    // N = 240, 176, 112
+// Column chunks the tuner tries for each player count and node count; the
+// first is the default (the widest chunk: fewest MMA rounds, one CTA per SM).
+template <int JJ, int NN> struct Chunks;
+template <int NN> struct Chunks<2, NN> { static constexpr int count = 1, v0 = NN, v1 = NN, v2 = NN; };  // N = n padded
+template <> struct Chunks<3, 5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };
+template <> struct Chunks<3, 9> { static constexpr int count = 2, v0 = 9, v1 = 3, v2 = 3; };
+template <> struct Chunks<3, 17> { static constexpr int count = 3, v0 = 9, v1 = 6, v2 = 3; };    // N = 160, 112, 64
+template <> struct Chunks<3, 33> { static constexpr int count = 3, v0 = 7, v1 = 5, v2 = 3; };    // N = 240, 176, 112
+template <> struct Chunks<4, 5> { static constexpr int count = 2, v0 = 5, v1 = 2, v2 = 2; };     // N = 160, 64
+template <> struct Chunks<4, 9> { static constexpr int count = 2, v0 = 2, v1 = 1, v2 = 1; };     // N = 192, 96
 
 // ---- helpers -------------------------------------------------------------------
 // T_0..T_{NN-1}(x) rounded to FP32, by the three-term recurrence carried in
@@ -173,40 +185,49 @@ __device__ __forceinline__ void split_store16(const float *v, uint8_t *dst, uint
     }
 }
 
-// the two other modes (a < b) of player i in a 3-player game
-__device__ __forceinline__ void other_modes(int i, int &a, int &b)
+// the other modes of player i in a J-player game, ascending: o[0] = a, then the rest
+template <int JJ>
+__device__ __forceinline__ void other_modes(int i, int (&o)[3])
 {
-    a = (i == 0) ? 1 : 0;
-    b = (i == 2) ? 1 : 2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = k < i ? k : k + 1;     // k-th mode other than i
+}
+
+// stride of mode s in a row-major tensor of J modes with NN entries each
+template <int JJ, int NN>
+__host__ __device__ constexpr int mode_stride(int s)
+{
+    int r = 1;
+    for (int t = s + 1; t < JJ; ++t) r *= NN;
+    return r;
 }
 
 // ---- B operand: split C_i once per iteration -----------------------------------
 // Thread per (instance, player, chunk, row of the chunk, 16-byte K chunk).
-template <int FORM, int NN, int CH>
+template <int FORM, int JJ, int NN, int CH>
 __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameStat *__restrict__ stats, int B)
 {
-    using S = Shape<FORM, NN, CH>;
+    using S = Shape<FORM, JJ, NN, CH>;
     using F = GForm<FORM>;
     const int per_item = S::NC * S::KC;
-    const int64_t total = (int64_t)B * 3 * S::NCH * per_item;
+    const int64_t total = (int64_t)B * JJ * S::NCH * per_item;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % per_item);
         const int64_t it = t / per_item;
         const int c = (int)(it % S::NCH);
-        const int i = (int)((it / S::NCH) % 3);
-        const int q = (int)(it / (S::NCH * 3));
+        const int i = (int)((it / S::NCH) % JJ);
+        const int q = (int)(it / (S::NCH * JJ));
         if (stats[q].done || stats[q].mode != 1) continue;
         const GameDev &g = insts[q];
         const int row = e / S::KC, kc = e - row * S::KC;
-        int a, b;
-        other_modes(i, a, b);
-        const int si = i == 0 ? NN * NN : i == 1 ? NN : 1;
-        const int sa = a == 0 ? NN * NN : a == 1 ? NN : 1;
-        const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
+        int o[3] = {0, 0, 0};
+        other_modes<JJ>(i, o);
+        const int si = mode_stride<JJ, NN>(i), sa = mode_stride<JJ, NN>(o[0]);
         const double *C = g.C + (size_t)i * g.NP;
         float v[S::E];
         if (row < S::TCOL) {
-            // tail column k_l: C[k_i, k_a, n-1]
+            // tail column k_l (J = 3): C[k_i, k_a, n-1]
+            const int sb = mode_stride<JJ, NN>(o[1]);
             const int ki = c * S::CHKI + row;
 #pragma unroll
             for (int k = 0; k < S::E; ++k) {
@@ -216,12 +237,28 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
             }
         } else {
             const int mrow = row - S::TCOL;
-            const int kl = mrow / S::NBP, kb = mrow - kl * S::NBP;
-            const int ki = c * S::CHKI + kl;
+            int ki, roff;
+            bool ok;
+            if constexpr (JJ == 2) {
+                ki = c * S::CHKI + mrow;
+                roff = 0;
+                ok = mrow < S::CHKI && ki < NN;
+            } else if constexpr (JJ == 3) {
+                const int kl = mrow / S::NBP, kb = mrow - kl * S::NBP;
+                ki = c * S::CHKI + kl;
+                roff = kb * mode_stride<JJ, NN>(o[1]);
+                ok = ki < NN && kb < S::NM;
+            } else {
+                const int kl = mrow / S::NBP, rr = mrow - kl * S::NBP;
+                ki = c * S::CHKI + kl;
+                const int kb = rr / NN, kcc = rr - kb * NN;
+                roff = kb * mode_stride<JJ, NN>(o[1]) + kcc * mode_stride<JJ, NN>(o[2]);
+                ok = ki < NN && rr < NN * NN;
+            }
 #pragma unroll
             for (int k = 0; k < S::E; ++k) {
                 const int ka = kc * S::E + k;
-                v[k] = (ki < NN && kb < S::NM && ka < S::NM) ? (float)C[ki * si + ka * sa + kb * sb] : 0.0f;
+                v[k] = (ok && ka < S::NM) ? (float)C[ki * si + ka * sa + roff] : 0.0f;
             }
         }
         uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES + (size_t)c * S::CHUNK_BYTES +
@@ -229,20 +266,18 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
         split_store16<FORM, F::SB>(v, dst, S::SPLIT_BYTES);
     }
     if constexpr (S::TAIL) {
-        // the FP32 tail coefficients, after each player's chunks
-        const int64_t ttot = (int64_t)B * 3 * S::TAIL_FLOATS;
+        // the FP32 tail coefficients (J = 3), after each player's chunks
+        const int64_t ttot = (int64_t)B * JJ * S::TAIL_FLOATS;
         for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ttot;
              t += (int64_t)gridDim.x * blockDim.x) {
             const int e = (int)(t % S::TAIL_FLOATS);
-            const int i = (int)((t / S::TAIL_FLOATS) % 3);
-            const int q = (int)(t / (S::TAIL_FLOATS * 3));
+            const int i = (int)((t / S::TAIL_FLOATS) % JJ);
+            const int q = (int)(t / (S::TAIL_FLOATS * JJ));
             if (stats[q].done || stats[q].mode != 1) continue;
             const GameDev &g = insts[q];
-            int a, b;
-            other_modes(i, a, b);
-            const int si = i == 0 ? NN * NN : i == 1 ? NN : 1;
-            const int sa = a == 0 ? NN * NN : a == 1 ? NN : 1;
-            const int sb = b == 0 ? NN * NN : b == 1 ? NN : 1;
+            int o[3] = {0, 0, 0};
+            other_modes<JJ>(i, o);
+            const int si = mode_stride<JJ, NN>(i), sa = mode_stride<JJ, NN>(o[0]), sb = mode_stride<JJ, NN>(o[1]);
             const double *C = g.C + (size_t)i * g.NP;
             const int ki = e / S::CAP, k = e - ki * S::CAP;
             const float v = k < NN ? (float)C[ki * si + (NN - 1) * sa + k * sb] : 0.0f;   // Ca[ki][kb = k]
@@ -278,11 +313,11 @@ __device__ __forceinline__ void objective_f32(const float (&w)[NN], float xc, fl
     W2 = -h + delta * slope * slope * s2;
 }
 
-template <int FORM, int NN, int CH>
-__global__ void __launch_bounds__(kThreads, (Shape<FORM, NN, CH>::MINB))
+template <int FORM, int JJ, int NN, int CH>
+__global__ void __launch_bounds__(kThreads, (Shape<FORM, JJ, NN, CH>::MINB))
 game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats, int B, int *err)
 {
-    using S = Shape<FORM, NN, CH>;
+    using S = Shape<FORM, JJ, NN, CH>;
     using F = GForm<FORM>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;                                         // SA x [128 x KP]
@@ -312,9 +347,9 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int NP = NN * NN * NN;
+    constexpr int NP = S::NPOW;
     const int tiles = (NP + kTile - 1) / kTile;
-    const int64_t items = (int64_t)B * 3 * tiles;
+    const int64_t items = (int64_t)B * JJ * tiles;
     // producer-thread state (tid == kProducer)
     uint32_t ld_phase = 0;     // bit s: parity of B stage s
     uint32_t pending = 0;      // bit s: a copy into stage s is in flight
@@ -329,7 +364,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     // in split precision (uniform across the block)
     auto next_item = [&](int64_t from) {
         for (int64_t it = from; it < items; it += gridDim.x) {
-            const int q = (int)(it / (tiles * 3));
+            const int q = (int)(it / (tiles * JJ));
             if (!stats[q].done && stats[q].mode == 1) return it;
         }
         return items;
@@ -339,7 +374,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     auto issue_mma = [&](int c) {
         const int stage = c & 1;
         const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;
-        const int N = S::TCOL + kis * S::NBP;
+        // MMA N: a multiple of 16 (J = 2 stores the k_i of its one chunk padded to NC)
+        const int N = JJ == 2 ? S::NC : S::TCOL + kis * S::NBP;
         // a copy whose wait gave up stays pending: the exit path waits for it
         if (mbar_wait_bounded(&bars[stage], (ld_phase >> stage) & 1u, err)) {
             ld_phase ^= 1u << stage;
@@ -375,11 +411,12 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     // epilogue, and chunk 0's MMA is issued.
     auto prologue = [&](int64_t it) {
         const int t = (int)(it % tiles);
-        const int i = (int)((it / tiles) % 3);
-        const int q = (int)(it / (tiles * 3));
+        const int i = (int)((it / tiles) % JJ);
+        const int q = (int)(it / (tiles * JJ));
         const GameDev &g = insts[q];
-        int a, b;
-        other_modes(i, a, b);
+        int o[3] = {0, 0, 0};
+        other_modes<JJ>(i, o);
+        const int a = o[0];
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
         if (tid == kProducer)
             for (int c = 0; c < 2 && c < S::NCH; ++c) {
@@ -394,16 +431,30 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         }
         const int j = t * kTile + row;
         const bool valid = j < NP;
-        float Ta[NN], Tbn[NN];
+        float Ta[NN];
         const double xa = valid ? g.X[a * NP + j] : 0.0;
-        const double xb = valid ? g.X[b * NP + j] : 0.0;
         cheb_row_f32<NN>(xa, Ta);
-        cheb_row_f32<NN>(xb, Tbn);
+        if constexpr (JJ == 3) {
+            float Tbn[NN];
+            const double xb = valid ? g.X[o[1] * NP + j] : 0.0;
+            cheb_row_f32<NN>(xb, Tbn);
 #pragma unroll
-        for (int k = 0; k < S::NM; ++k) tb_s[k * kTile + row] = valid ? Tbn[k] : 0.0f;
-        if constexpr (S::TAIL) {
-            tb_s[S::NM * kTile + row] = valid ? Ta[NN - 1] : 0.0f;
-            tb_s[(S::NM + 1) * kTile + row] = valid ? Tbn[NN - 1] : 0.0f;
+            for (int k = 0; k < S::NM; ++k) tb_s[k * kTile + row] = valid ? Tbn[k] : 0.0f;
+            if constexpr (S::TAIL) {
+                tb_s[S::NM * kTile + row] = valid ? Ta[NN - 1] : 0.0f;
+                tb_s[(S::NM + 1) * kTile + row] = valid ? Tbn[NN - 1] : 0.0f;
+            }
+        } else if constexpr (JJ == 4) {
+            float Tbn[NN], Tcn[NN];
+            const double xb = valid ? g.X[o[1] * NP + j] : 0.0;
+            const double xc = valid ? g.X[o[2] * NP + j] : 0.0;
+            cheb_row_f32<NN>(xb, Tbn);
+            cheb_row_f32<NN>(xc, Tcn);
+#pragma unroll
+            for (int k = 0; k < NN; ++k) {
+                tb_s[k * kTile + row] = valid ? Tbn[k] : 0.0f;
+                tb_s[(NN + k) * kTile + row] = valid ? Tcn[k] : 0.0f;
+            }
         }
 #pragma unroll
         for (int kc = 0; kc < S::KC; ++kc) {
@@ -427,17 +478,26 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     tc_fence_after();
     while (item < items) {
         const int t = (int)(item % tiles);
-        const int i = (int)((item / tiles) % 3);
-        const int q = (int)(item / (tiles * 3));
+        const int i = (int)((item / tiles) % JJ);
+        const int q = (int)(item / (tiles * JJ));
         GameStat *st = &stats[q];
         const GameDev &g = insts[q];
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
         const int j = t * kTile + row;
         const bool valid = j < NP;
-        // the epilogue factor T_{k_b}(x_b(j)) of this thread's row, from the stage
-        float Tb[S::NBP];
+        // the epilogue factors of this thread's row, from the stage: J = 3
+        // T_{k_b}(x_b(j)); J = 4 T_{k_b}(x_b(j)) and T_{k_c}(x_c(j))
+        constexpr int NTB = JJ == 3 ? S::NBP : 1;
+        float Tb[NTB];
 #pragma unroll
-        for (int k = 0; k < S::NBP; ++k) Tb[k] = (k < S::NM) ? tb_s[k * kTile + row] : 0.0f;
+        for (int k = 0; k < NTB; ++k) Tb[k] = (JJ == 3 && k < S::NM) ? tb_s[k * kTile + row] : 0.0f;
+        constexpr int N4 = JJ == 4 ? NN : 1;
+        float Tb4[N4], Tc4[N4];
+#pragma unroll
+        for (int k = 0; k < N4; ++k) {
+            Tb4[k] = JJ == 4 ? tb_s[k * kTile + row] : 0.0f;
+            Tc4[k] = JJ == 4 ? tb_s[(NN + k) * kTile + row] : 0.0f;
+        }
         float ta_last = 0.0f, tb_last = 0.0f;    // T_{n-1}(x_a), T_{n-1}(x_b) (TAIL)
         if constexpr (S::TAIL) {
             ta_last = tb_s[S::NM * kTile + row];
@@ -464,7 +524,40 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
             }
             // epilogue: rows 32 quarter + lane (the row whose T_b this thread
             // holds), k_i of this chunk alternating between the two halves
-            {
+            if constexpr (JJ == 2) {
+                // the columns are the k_i themselves
+                const int r = quarter * 32 + lane;
+                const uint32_t lane_addr = tmem + (uint32_t)(buf * S::TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
+                for (int g16 = ehalf; g16 < S::NC / 16; g16 += 2) {
+                    uint32_t v[16];
+                    tmem_ld16(lane_addr + g16 * 16, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int col = g16 * 16 + e;
+                        if (col < kis) w_s[(c * S::CHKI + col) * kTile + r] = __uint_as_float(v[e]);
+                    }
+                }
+            } else if constexpr (JJ == 4) {
+                // w[k_i] = sum_{k_b, k_c} Y[(k_i, k_b, k_c)] T_{k_b}(x_b) T_{k_c}(x_c)
+                const int r = quarter * 32 + lane;
+                const uint32_t lane_addr = tmem + (uint32_t)(buf * S::TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
+                for (int kl = ehalf; kl < kis; kl += 2) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int g16 = 0; g16 < S::NBP / 16; ++g16) {
+                        uint32_t v[16];
+                        tmem_ld16(lane_addr + kl * S::NBP + g16 * 16, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int rr = g16 * 16 + e;
+                            if (rr < NN * NN) acc = fmaf(__uint_as_float(v[e]), Tb4[rr / N4] * Tc4[rr % N4], acc);
+                        }
+                    }
+                    w_s[(c * S::CHKI + kl) * kTile + r] = acc;
+                }
+            } else {
                 const int r = quarter * 32 + lane;
                 const uint32_t lane_addr = tmem + (uint32_t)(buf * S::TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
                 for (int kl = ehalf; kl < kis; kl += 2) {
@@ -510,9 +603,9 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 float w[NN];
 #pragma unroll
                 for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
-                // the node's own coordinate (j = j_0 n^2 + j_1 n + j_2) and the
-                // per-player constants formed on the host
-                const int ki = i == 0 ? j / (NN * NN) : i == 1 ? (j / NN) % NN : j % NN;
+                // the node's own coordinate (row-major multi-index, last player
+                // fastest) and the per-player constants formed on the host
+                const int ki = (j / mode_stride<JJ, NN>(i)) % NN;
                 const double pbi = 0.5 * g.P_M * (g.nodes[ki] + 1.0);
                 const double ui = g.u[i * NP + j];
                 const double slope = g.slope[i];
@@ -606,11 +699,11 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 }
 
 // Most CTAs of one variant that fit on an SM (shared memory, registers, TMEM).
-template <int FORM, int NN, int CH>
+template <int FORM, int JJ, int NN, int CH>
 cheb_status max_ctas(int *out)
 {
-    using S = Shape<FORM, NN, CH>;
-    auto kern = game_player_tc_kernel<FORM, NN, CH>;
+    using S = Shape<FORM, JJ, NN, CH>;
+    auto kern = game_player_tc_kernel<FORM, JJ, NN, CH>;
     static PerDevice cache;
     return per_device_once(cache, [kern](int *v) -> cheb_status {
         CHEB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
@@ -626,29 +719,28 @@ cheb_status max_ctas(int *out)
     }, out);
 }
 
-template <int FORM, int NN, int CH>
+template <int FORM, int JJ, int NN, int CH>
 cheb_status launch_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int per_sm, cudaStream_t st)
 {
-    using S = Shape<FORM, NN, CH>;
+    using S = Shape<FORM, JJ, NN, CH>;
     static_assert(S::SMEM <= 227 * 1024, "game player tile does not fit in shared memory");
     int kmax = 1;
-    cheb_status r = max_ctas<FORM, NN, CH>(&kmax);
+    cheb_status r = max_ctas<FORM, JJ, NN, CH>(&kmax);
     if (r) return r;
     per_sm = std::max(1, std::min(per_sm, kmax));
+    const std::string shape = "J=" + std::to_string(JJ) + " n=" + std::to_string(NN) + " chunk=" + std::to_string(CH);
     {
-        const int64_t total = (int64_t)B * 3 * S::NCH * S::NC * S::KC;
+        const int64_t total = (int64_t)B * JJ * S::NCH * S::NC * S::KC;
         const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-        ProfScope prof("game_bprep n=" + std::to_string(NN) + " chunk=" + std::to_string(CH), st);
-        game_bprep_kernel<FORM, NN, CH><<<blocks, 256, 0, st>>>(d_inst, d_stat, B);
+        ProfScope prof("game_bprep " + shape, st);
+        game_bprep_kernel<FORM, JJ, NN, CH><<<blocks, 256, 0, st>>>(d_inst, d_stat, B);
         CHEB_CUDA_TRY(cudaGetLastError());
     }
-    const int tiles = (NN * NN * NN + kTile - 1) / kTile;
-    const int64_t items = (int64_t)B * 3 * tiles;
+    const int tiles = (S::NPOW + kTile - 1) / kTile;
+    const int64_t items = (int64_t)B * JJ * tiles;
     const int grid = (int)std::min<int64_t>(items, (int64_t)ctx->num_sms * per_sm);
-    ProfScope prof("game_player_tc n=" + std::to_string(NN) + " chunk=" + std::to_string(CH) +
-                       " ctas/SM=" + std::to_string(per_sm),
-                   st);
-    game_player_tc_kernel<FORM, NN, CH><<<grid, kThreads, S::SMEM, st>>>(d_inst, d_stat, B, ctx->d_error);
+    ProfScope prof("game_player_tc " + shape + " ctas/SM=" + std::to_string(per_sm), st);
+    game_player_tc_kernel<FORM, JJ, NN, CH><<<grid, kThreads, S::SMEM, st>>>(d_inst, d_stat, B, ctx->d_error);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
@@ -656,26 +748,30 @@ cheb_status launch_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat
 // A tile configuration: chunk variant c (index into Chunks<NN>) and CTAs per SM k.
 constexpr int cfg_of(int c, int k) { return c * 4 + k; }
 
-template <int FORM, int NN>
+template <int FORM, int JJ, int NN>
 cheb_status run_cfg(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int cfg, cudaStream_t st)
 {
-    using C = Chunks<NN>;
+    using C = Chunks<JJ, NN>;
     const int c = cfg / 4, k = cfg % 4;
-    if (c == 1 && C::count > 1) return launch_player<FORM, NN, C::v1>(ctx, d_inst, d_stat, B, k, st);
-    if (c == 2 && C::count > 2) return launch_player<FORM, NN, C::v2>(ctx, d_inst, d_stat, B, k, st);
-    return launch_player<FORM, NN, C::v0>(ctx, d_inst, d_stat, B, k, st);
+    if constexpr (C::count > 1)
+        if (c == 1) return launch_player<FORM, JJ, NN, C::v1>(ctx, d_inst, d_stat, B, k, st);
+    if constexpr (C::count > 2)
+        if (c == 2) return launch_player<FORM, JJ, NN, C::v2>(ctx, d_inst, d_stat, B, k, st);
+    return launch_player<FORM, JJ, NN, C::v0>(ctx, d_inst, d_stat, B, k, st);
 }
 
 // The configurations the tuner tries for NN: every chunk variant at every CTA
 // count from 1 to what fits.
-template <int FORM, int NN>
+template <int FORM, int JJ, int NN>
 cheb_status candidates(std::vector<int> *out)
 {
-    using C = Chunks<NN>;
+    using C = Chunks<JJ, NN>;
     int k[3] = {1, 1, 1};
-    cheb_status r = max_ctas<FORM, NN, C::v0>(&k[0]);
-    if (!r && C::count > 1) r = max_ctas<FORM, NN, C::v1>(&k[1]);
-    if (!r && C::count > 2) r = max_ctas<FORM, NN, C::v2>(&k[2]);
+    cheb_status r = max_ctas<FORM, JJ, NN, C::v0>(&k[0]);
+    if constexpr (C::count > 1)
+        if (!r) r = max_ctas<FORM, JJ, NN, C::v1>(&k[1]);
+    if constexpr (C::count > 2)
+        if (!r) r = max_ctas<FORM, JJ, NN, C::v2>(&k[2]);
     if (r) return r;
     out->clear();
     for (int c = 0; c < C::count; ++c)
@@ -683,113 +779,111 @@ cheb_status candidates(std::vector<int> *out)
     return CHEB_OK;
 }
 
-template <int FORM, int NN>
+template <int FORM, int JJ, int NN>
 std::string describe(int cfg)
 {
-    using C = Chunks<NN>;
+    using C = Chunks<JJ, NN>;
     const int c = cfg / 4, chunk = c == 0 ? C::v0 : c == 1 ? C::v1 : C::v2;
-    constexpr int nbp = Shape<FORM, NN, C::v0>::NBP;
-    constexpr int tcol = Shape<FORM, NN, C::v0>::TCOL;
-    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(tcol + chunk * nbp) +
-           ") ctas/SM=" + std::to_string(cfg % 4);
+    const int N = c == 0 ? Shape<FORM, JJ, NN, C::v0>::NC : c == 1 ? Shape<FORM, JJ, NN, C::v1>::NC
+                                                                   : Shape<FORM, JJ, NN, C::v2>::NC;
+    return "chunk=" + std::to_string(chunk) + " (N=" + std::to_string(N) + ") ctas/SM=" + std::to_string(cfg % 4);
+}
+
+// the (J, n) combinations of the split player update
+#define CHEB_GAME_TC_SHAPES(X) X(2, 5) X(2, 9) X(2, 17) X(2, 33) X(3, 5) X(3, 9) X(3, 17) X(3, 33) X(4, 5) X(4, 9)
+
+bool shape_ok(int J, int n)
+{
+#define CHEB_X(JJ, NN) if (J == JJ && n == NN) return true;
+    CHEB_GAME_TC_SHAPES(CHEB_X)
+#undef CHEB_X
+    return false;
 }
 
 template <int FORM>
-cheb_status dispatch_n(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, int cfg, cudaStream_t st)
+cheb_status dispatch_n(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int J, int n, int cfg,
+                       cudaStream_t st)
 {
-    switch (n) {
-    case 5: return run_cfg<FORM, 5>(ctx, d_inst, d_stat, B, cfg, st);
-    case 9: return run_cfg<FORM, 9>(ctx, d_inst, d_stat, B, cfg, st);
-    case 17: return run_cfg<FORM, 17>(ctx, d_inst, d_stat, B, cfg, st);
-    case 33: return run_cfg<FORM, 33>(ctx, d_inst, d_stat, B, cfg, st);
-    default: return fail(CHEB_EUNSUPPORTED, "game_solve: split precision supports n in {5, 9, 17, 33}");
-    }
+#define CHEB_X(JJ, NN) if (J == JJ && n == NN) return run_cfg<FORM, JJ, NN>(ctx, d_inst, d_stat, B, cfg, st);
+    CHEB_GAME_TC_SHAPES(CHEB_X)
+#undef CHEB_X
+    return fail(CHEB_EUNSUPPORTED, "game_solve: no split player update for this (J, n)");
 }
 
 template <int FORM>
-cheb_status candidates_n(int n, std::vector<int> *out)
+cheb_status candidates_n(int J, int n, std::vector<int> *out)
 {
-    switch (n) {
-    case 5: return candidates<FORM, 5>(out);
-    case 9: return candidates<FORM, 9>(out);
-    case 17: return candidates<FORM, 17>(out);
-    case 33: return candidates<FORM, 33>(out);
-    default: return fail(CHEB_EUNSUPPORTED, "game_solve: split precision supports n in {5, 9, 17, 33}");
-    }
+#define CHEB_X(JJ, NN) if (J == JJ && n == NN) return candidates<FORM, JJ, NN>(out);
+    CHEB_GAME_TC_SHAPES(CHEB_X)
+#undef CHEB_X
+    return fail(CHEB_EUNSUPPORTED, "game_solve: no split player update for this (J, n)");
 }
 
 template <int FORM>
-std::string describe_n(int n, int cfg)
+std::string describe_n(int J, int n, int cfg)
 {
-    switch (n) {
-    case 5: return describe<FORM, 5>(cfg);
-    case 9: return describe<FORM, 9>(cfg);
-    case 17: return describe<FORM, 17>(cfg);
-    default: return describe<FORM, 33>(cfg);
-    }
+#define CHEB_X(JJ, NN) if (J == JJ && n == NN) return describe<FORM, JJ, NN>(cfg);
+    CHEB_GAME_TC_SHAPES(CHEB_X)
+#undef CHEB_X
+    return "?";
 }
 
-template <int FORM, int NN, int CH> constexpr size_t variant_bytes()
+template <int FORM, int JJ, int NN> constexpr size_t max_bytes()
 {
-    return Shape<FORM, NN, CH>::PLAYER_BYTES;
-}
-
-template <int FORM, int NN> constexpr size_t max_bytes()
-{
-    using C = Chunks<NN>;
-    size_t b = variant_bytes<FORM, NN, C::v0>();
-    b = std::max(b, variant_bytes<FORM, NN, C::v1>());
-    return std::max(b, variant_bytes<FORM, NN, C::v2>());
+    using C = Chunks<JJ, NN>;
+    size_t b = Shape<FORM, JJ, NN, C::v0>::PLAYER_BYTES;
+    b = std::max(b, Shape<FORM, JJ, NN, C::v1>::PLAYER_BYTES);
+    return std::max(b, Shape<FORM, JJ, NN, C::v2>::PLAYER_BYTES);
 }
 
 // B-operand bytes per player, the largest over the chunk variants (the
 // workspace serves whichever variant runs)
-size_t bsplit_bytes(int n, int prec)
+template <int FORM>
+size_t bsplit_bytes_form(int J, int n)
 {
-#define CHEB_BS(FORM)                                   \
-    switch (n) {                                      \
-    case 5: return max_bytes<FORM, 5>();              \
-    case 9: return max_bytes<FORM, 9>();              \
-    case 17: return max_bytes<FORM, 17>();            \
-    case 33: return max_bytes<FORM, 33>();            \
-    default: return 0;                                \
-    }
-    switch (prec) {
-    case CHEB_BF16X3: CHEB_BS(CHEB_BF16X3)
-    case CHEB_BF16X6: CHEB_BS(CHEB_BF16X6)
-    case CHEB_TF32X3: CHEB_BS(CHEB_TF32X3)
-    default: return 0;
-    }
-#undef CHEB_BS
+#define CHEB_X(JJ, NN) if (J == JJ && n == NN) return max_bytes<FORM, JJ, NN>();
+    CHEB_GAME_TC_SHAPES(CHEB_X)
+#undef CHEB_X
+    return 0;
 }
 
-cheb_status run_any(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int n, int prec, int cfg,
+size_t bsplit_bytes(int J, int n, int prec)
+{
+    switch (prec) {
+    case CHEB_BF16X3: return bsplit_bytes_form<CHEB_BF16X3>(J, n);
+    case CHEB_BF16X6: return bsplit_bytes_form<CHEB_BF16X6>(J, n);
+    case CHEB_TF32X3: return bsplit_bytes_form<CHEB_TF32X3>(J, n);
+    default: return 0;
+    }
+}
+
+cheb_status run_any(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int J, int n, int prec, int cfg,
                     cudaStream_t st)
 {
     switch (prec) {
-    case CHEB_BF16X3: return dispatch_n<CHEB_BF16X3>(ctx, d_inst, d_stat, B, n, cfg, st);
-    case CHEB_BF16X6: return dispatch_n<CHEB_BF16X6>(ctx, d_inst, d_stat, B, n, cfg, st);
-    case CHEB_TF32X3: return dispatch_n<CHEB_TF32X3>(ctx, d_inst, d_stat, B, n, cfg, st);
+    case CHEB_BF16X3: return dispatch_n<CHEB_BF16X3>(ctx, d_inst, d_stat, B, J, n, cfg, st);
+    case CHEB_BF16X6: return dispatch_n<CHEB_BF16X6>(ctx, d_inst, d_stat, B, J, n, cfg, st);
+    case CHEB_TF32X3: return dispatch_n<CHEB_TF32X3>(ctx, d_inst, d_stat, B, J, n, cfg, st);
     default: return fail(CHEB_EINVAL, "game_solve: bad precision");
     }
 }
 
-cheb_status candidates_any(int n, int prec, std::vector<int> *out)
+cheb_status candidates_any(int J, int n, int prec, std::vector<int> *out)
 {
     switch (prec) {
-    case CHEB_BF16X3: return candidates_n<CHEB_BF16X3>(n, out);
-    case CHEB_BF16X6: return candidates_n<CHEB_BF16X6>(n, out);
-    case CHEB_TF32X3: return candidates_n<CHEB_TF32X3>(n, out);
+    case CHEB_BF16X3: return candidates_n<CHEB_BF16X3>(J, n, out);
+    case CHEB_BF16X6: return candidates_n<CHEB_BF16X6>(J, n, out);
+    case CHEB_TF32X3: return candidates_n<CHEB_TF32X3>(J, n, out);
     default: return fail(CHEB_EINVAL, "game_solve: bad precision");
     }
 }
 
-std::string describe_any(int n, int prec, int cfg)
+std::string describe_any(int J, int n, int prec, int cfg)
 {
     switch (prec) {
-    case CHEB_BF16X3: return describe_n<CHEB_BF16X3>(n, cfg);
-    case CHEB_BF16X6: return describe_n<CHEB_BF16X6>(n, cfg);
-    default: return describe_n<CHEB_TF32X3>(n, cfg);
+    case CHEB_BF16X3: return describe_n<CHEB_BF16X3>(J, n, cfg);
+    case CHEB_BF16X6: return describe_n<CHEB_BF16X6>(J, n, cfg);
+    default: return describe_n<CHEB_TF32X3>(J, n, cfg);
     }
 }
 
@@ -809,25 +903,28 @@ int batch_class(int B)
     return c;
 }
 
-std::string tune_key(int prec, int n, int B)
+std::string tune_key(int prec, int J, int n, int B)
 {
-    return std::string(form_name(prec)) + " n=" + std::to_string(n) + " batch class " + std::to_string(batch_class(B));
+    return std::string(form_name(prec)) + " J=" + std::to_string(J) + " n=" + std::to_string(n) + " batch class " +
+           std::to_string(batch_class(B));
 }
 
 }  // namespace
 
+bool tc_shape_supported(int J, int n) { return shape_ok(J, n); }
+
 size_t game_tc_workspace_bytes(int J, int n, int NP, int B, int prec)
 {
     (void)NP;
-    if (prec == CHEB_FP64 || J != 3) return 0;
-    return (size_t)B * 3 * ((bsplit_bytes(n, prec) + 255) & ~size_t(255));
+    if (prec == CHEB_FP64 || prec == CHEB_DF64 || !shape_ok(J, n)) return 0;
+    return (size_t)B * J * ((bsplit_bytes(J, n, prec) + 255) & ~size_t(255));
 }
 
 void game_tc_bind(GameDev *hinst, int B, int J, int n, int NP, int prec, uint8_t *ws)
 {
     (void)NP;
-    if (prec == CHEB_FP64 || J != 3) return;
-    const size_t per = 3 * ((bsplit_bytes(n, prec) + 255) & ~size_t(255));
+    if (prec == CHEB_FP64 || prec == CHEB_DF64 || !shape_ok(J, n)) return;
+    const size_t per = J * ((bsplit_bytes(J, n, prec) + 255) & ~size_t(255));
     for (int q = 0; q < B; ++q) hinst[q].bsplit = ws + per * q;
 }
 
@@ -837,31 +934,31 @@ cheb_status game_tc_player(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_sta
     (void)hinst;
     (void)NP;
     (void)ws;
-    if (J != 3) return fail(CHEB_EUNSUPPORTED, "game_solve: split precision needs J = 3");
+    if (!tc_shape_supported(J, n)) return fail(CHEB_EUNSUPPORTED, "game_solve: no split player update for this (J, n)");
     int cfg = cfg_of(0, 1);   // the default shape
     if (ctx->tune_mode >= 2) {
         std::vector<int> cands;
-        cheb_status r = candidates_any(n, prec, &cands);
+        cheb_status r = candidates_any(J, n, prec, &cands);
         if (r) return r;
         cfg = ctx->tune_mode - 2;
         if (std::find(cands.begin(), cands.end(), cfg) == cands.end())
             return fail(CHEB_EINVAL, "game_solve: the forced tile configuration does not exist for n = " +
                                          std::to_string(n));
     } else if (ctx->tune_mode == 0) {
-        auto it = ctx->game_tune.find(tune_key(prec, n, B));
+        auto it = ctx->game_tune.find(tune_key(prec, J, n, B));
         if (it != ctx->game_tune.end()) cfg = it->second.first;
     }
-    return run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st);
+    return run_any(ctx, d_inst, d_stat, B, J, n, prec, cfg, st);
 }
 
 cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat, int B, int J, int n, int prec,
                          cudaStream_t st)
 {
-    if (prec == CHEB_FP64 || J != 3 || ctx->tune_mode != 0) return CHEB_OK;
-    const std::string key = tune_key(prec, n, B);
+    if (prec == CHEB_FP64 || !tc_shape_supported(J, n) || ctx->tune_mode != 0) return CHEB_OK;
+    const std::string key = tune_key(prec, J, n, B);
     if (ctx->game_tune.count(key)) return CHEB_OK;
     std::vector<int> cands;
-    cheb_status r = candidates_any(n, prec, &cands);
+    cheb_status r = candidates_any(J, n, prec, &cands);
     if (r) return r;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CHEB_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
@@ -874,9 +971,9 @@ cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat,
     std::string times;
     for (size_t c = 0; c < cands.size() && r == CHEB_OK; ++c) {
         const int cfg = cands[c];
-        if ((r = run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st))) break;   // warm-up
+        if ((r = run_any(ctx, d_inst, d_stat, B, J, n, prec, cfg, st))) break;   // warm-up
         cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 3 && r == CHEB_OK; ++rep) r = run_any(ctx, d_inst, d_stat, B, n, prec, cfg, st);
+        for (int rep = 0; rep < 3 && r == CHEB_OK; ++rep) r = run_any(ctx, d_inst, d_stat, B, J, n, prec, cfg, st);
         cudaEventRecord(e1, st);
         if (r) break;
         cudaError_t ce = cudaEventSynchronize(e1);
@@ -889,7 +986,7 @@ cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat,
         ms /= 3.0f;
         char buf[64];
         std::snprintf(buf, sizeof(buf), " %.1f us", 1000.0f * ms);
-        times += (c ? ", " : "") + describe_any(n, prec, cfg) + buf;
+        times += (c ? ", " : "") + describe_any(J, n, prec, cfg) + buf;
         if (c == 0 || ms < best_ms) {
             best_ms = ms;
             best = cfg;
@@ -898,7 +995,7 @@ cheb_status game_tc_tune(cheb_ctx *ctx, const GameDev *d_inst, GameStat *d_stat,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r) return r;
-    ctx->game_tune[key] = {best, describe_any(n, prec, best) + " [tried: " + times + "]"};
+    ctx->game_tune[key] = {best, describe_any(J, n, prec, best) + " [tried: " + times + "]"};
     return CHEB_OK;
 }
 

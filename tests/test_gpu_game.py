@@ -270,7 +270,10 @@ def test_diverging_warm_start_falls_back_to_cold(ctx):
     (3, 9, "fp64", (0, 2), (2, 1, 0), 1e-12),
     (4, 5, "fp64", (2, 3), (0, 1, 3, 2), 1e-12),
     (3, 17, "bf16x6", (0, 2), (2, 1, 0), 2e-5),
-    (3, 33, "tf32x3", (0, 2), (2, 1, 0), 2e-5)])
+    (3, 33, "tf32x3", (0, 2), (2, 1, 0), 2e-5),
+    (2, 17, "bf16x6", (0, 1), (1, 0), 2e-5),
+    (4, 9, "fp64", (2, 3), (0, 1, 3, 2), 1e-12),
+    (4, 9, "bf16x6", (2, 3), (0, 1, 3, 2), 2e-5)])
 def test_symmetric_players_on_gpu(ctx, J, n, prec, pair, perm, tol):
     """The symmetry invariants of Section 4's J = 2, 3, 4 examples on the converged
     GPU solves: V_i(p) = V_k(sigma p), u_i(p) = u_k(sigma p) for the symmetric pair
@@ -373,3 +376,56 @@ def test_mixed_size_split_batch_sampled_nodes_match_oracle(ctx, prec):
                 v_gpu = O.eval_direct(C2[i].reshape(n, n, n), xr)
                 assert abs(us - U2[i, j]) < 1e-5, (q, n, int(j), i, us, U2[i, j])
                 assert abs(vs - v_gpu) < tol_v * max(1.0, abs(vs)), (q, n, int(j), i, vs, v_gpu)
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("J,n", [(2, 5), (2, 9), (2, 17), (4, 5), (4, 9)])
+def test_split_iterations_close_to_oracle_two_and_four_players(ctx, J, n, prec):
+    """The split player update for J = 2 (the GEMM is the series itself) and J = 4 (two
+    rest modes reduced with T_{k_b} T_{k_c}): a few passes against the oracle's FP64
+    passes, with the bound of the J = 3 test."""
+    p = I.draw_game_params(I.SplitMix64(60 + J * 5 + n), J)
+    R = 3 if J == 4 and n == 9 else 6
+    V, u, res = cb.game_solve(ctx, p, cb.game_opts(n, tol=0.0, max_iter=R, prec=prec, polish_fp64=False),
+                              raise_on_error=False)
+    assert res[0].iters == R and res[0].iters_split == R
+    ref = O.game_solve(p, O.make_opts(n, tol=0.0, max_iter=R))
+    bound = R * (U_FORM[prec] + 2.0 ** -20) * 10
+    e = rel(V[0].cpu().numpy(), ref["Vcoef"])
+    print(f"split {prec} J={J} n={n} after {R} passes: coefficient error {e:.2e} (bound {bound:.1e})")
+    assert e < bound
+    assert np.abs(u[0].cpu().numpy() - ref["u"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("J,n", [(2, 17), (4, 9)])
+def test_split_sampled_node_updates_two_and_four_players(ctx, J, n):
+    """One split pass (BF16x6) from the GPU's own iterate against the oracle's Steps 1-3 at
+    sampled nodes: J = 2 at n = 17, J = 4 at n = 9 (N_P = 6,561, GEMM N = n^3 = 729)."""
+    p = I.draw_game_params(I.SplitMix64(70 + J), J)
+    R = 4
+    o1 = cb.game_opts(n, tol=0.0, max_iter=R - 1, prec="bf16x6", polish_fp64=False)
+    o2 = cb.game_opts(n, tol=0.0, max_iter=R, prec="bf16x6", polish_fp64=False)
+    V1, u1, _ = cb.game_solve(ctx, p, o1, raise_on_error=False)
+    V2, u2, _ = cb.game_solve(ctx, p, o2, raise_on_error=False)
+    C1, U1 = V1[0].cpu().numpy(), u1[0].cpu().numpy()
+    C2, U2 = V2[0].cpu().numpy(), u2[0].cpu().numpy()
+    opts = O.make_opts(n, tol=0.0, max_iter=R)
+    rng = np.random.default_rng(J)
+    for j in rng.choice(n ** J, 8, replace=False):
+        pb, xr = _node(opts, J, j)
+        for i in range(J):
+            us, vs, inside, conc = O.game_node_update(p, opts, i, pb, U1[:, j], C1[i])
+            v_gpu = O.eval_direct(C2[i].reshape((n,) * J), xr)
+            assert abs(us - U2[i, j]) < 1e-5, (int(j), i, us, U2[i, j])
+            assert abs(vs - v_gpu) < 50 * (U_FORM["bf16x6"] + 2.0 ** -20) * max(1.0, abs(vs)), (int(j), i)
+
+
+def test_split_two_players_full_solve_with_polish(ctx):
+    """J = 2, n = 17 in BF16x6 to its floor, then polished in double-float to 1e-10, against
+    the FP64 solve (both within tol / (1 - delta_h) of the fixed point)."""
+    p = I.game_params(2)
+    Vf, _, rf = cb.game_solve(ctx, p, cb.game_opts(17, tol=1e-10, max_iter=20000, prec="fp64"))
+    V, _, r = cb.game_solve(ctx, p, cb.game_opts(17, tol=1e-10, max_iter=20000, prec="bf16x6", polish_fp64=True),
+                            raise_on_error=False)
+    assert r[0].status == 0 and r[0].residual < 1e-10 and r[0].iters_split > 0
+    assert rel(V[0].cpu().numpy(), Vf[0].cpu().numpy()) < 1e-6

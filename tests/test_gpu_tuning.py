@@ -44,7 +44,7 @@ def test_every_configuration_gives_identical_iterates(ctx, n):
         V, u, r = solve(ctx, p, [n])
         assert torch.equal(V[0], V0[0]) and torch.equal(u[0], u0[0])
         rep = ctx.tuning_report()
-        assert f"bf16x6 n={n} batch class 0" in rep and "tried" in rep
+        assert f"bf16x6 J=3 n={n} batch class 0" in rep and "tried" in rep
     finally:
         ctx.set_tuning(0)
 
@@ -61,7 +61,7 @@ def test_tuned_batch_matches_default(ctx):
         for q in range(len(params)):
             assert torch.equal(V[q], V0[q]) and torch.equal(u[q], u0[q])
         rep = ctx.tuning_report()
-        assert "tf32x3 n=9" in rep and "tf32x3 n=17" in rep
+        assert "tf32x3 J=3 n=9" in rep and "tf32x3 J=3 n=17" in rep
     finally:
         ctx.set_tuning(0)
 
