@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-game", action="store_true", help="skip the game-solve measurements")
     ap.add_argument("--no-batched", action="store_true", help="skip the 1,024-game batch (config 4)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned warm start (config 5)")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "surrogate", "paths"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "surrogate", "paths", "mlp"],
                     help="grid: the d=4 n=33 64^4 evaluation (default); batched: 1,024 uneven game solves")
     ap.add_argument("--count", type=int, default=1024, help="instances of the batched workload")
     ap.add_argument("--fp64-sample", type=int, default=24,
@@ -517,6 +517,7 @@ def run_ours(args):
             line["config4_batched"] = batched_results(args, ctx, rank, world, local)
         if world == 1 and not args.no_surrogate:
             line["config5_surrogate"] = surrogate_results(args, ctx)
+            line["config5_surrogate"]["training_throughput"] = training_throughput(args, ctx, epochs=5)
         if not args.no_cpu and world == 1:
             val, cores, sample, ref_slab = oracle_grid_sample(c_np, grid, target_s=10.0)
             gpu_slab = out[:4].double().cpu().numpy()
@@ -784,6 +785,75 @@ def surrogate_results(args, ctx):
     return line
 
 
+def training_throughput(args, ctx, epochs=None):
+    """Training throughput of the warm-start network of config 5 (8 -> 4 x 256 -> 2 x 4,913,
+    batch 256, 78 steps per epoch over 20,000 rows) on seeded synthetic inputs and targets:
+    the epoch graph timed with CUDA events, then one epoch with per-kernel events for the
+    share of the wide output layer's three products (forward, weight gradient, input
+    gradient: 2 x 256 x 9,826 x 256 FLOPs each). The step's working set (weights, packed
+    operands, activations: about 60 MB) stays in L2 by design."""
+    import torch
+    import paper_2307_04688_gb300 as cb
+    S, F, O, Bt = 20000, 8, 2 * 17 ** 3, 256
+    E = args.epochs if epochs is None else epochs
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((S, F), dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.randn((S, O), dtype=torch.float64, device="cuda", generator=g)
+    net = cb.Surrogate(ctx, F, 256, 4, O, seed=7)
+    net.train(X, Y, epochs=1, batch=Bt)
+    steps = E * (S // Bt)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    net.train(X, Y, epochs=E, batch=Bt)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    dims = [F, 256, 256, 256, 256, O]
+    flop_step = 3 * 2 * Bt * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    ctx.profile(True)
+    net.train(X, Y, epochs=1, batch=Bt)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    net.close()
+    sustained = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sustained = float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        sustained = 1700.0
+    per = S // Bt
+    layer = {}
+    big = 2.0 * Bt * O * 256
+    for name in (f"mlp_gemm M={Bt} N={O} K=256", f"mlp_gemm M={O} N=256 K={Bt}", f"mlp_gemm M={Bt} N=256 K={O}"):
+        if name in prof:
+            n, t = prof[name]
+            tf = big * n / (t * 1e-3) / 1e12
+            layer[name] = {"us": 1e3 * t / n, "tflops": tf, "frac_of_sustained_bf16": tf / sustained}
+    tot_big = sum(v["us"] for v in layer.values())
+    out = {"workload": f"8 -> 4 x 256 -> {O} GELU network, batch {Bt}, {S} rows, {E} epochs, synthetic (seed 5)",
+           "ms_per_step": ms / steps, "steps_per_s": steps / (ms * 1e-3),
+           "network_tflops": flop_step * steps / (ms * 1e-3) / 1e12,
+           "network_frac_of_sustained_bf16": flop_step * steps / (ms * 1e-3) / 1e12 / sustained,
+           "wide_layer": layer,
+           "wide_layer_tflops": 3 * big / (tot_big * 1e-6) / 1e12 if layer else None,
+           "wide_layer_frac_of_sustained_bf16": (3 * big / (tot_big * 1e-6) / 1e12 / sustained) if layer else None,
+           "kernel_us_per_step": {k: 1e3 * v[1] / per for k, v in sorted(prof.items(), key=lambda x: -x[1][1])},
+           "launches_per_step": sum(v[0] for v in prof.values()) / per,
+           "peak": {"bf16_tflops_sustained": sustained, "source": "measured"}}
+    return out
+
+
+def run_mlp(args):
+    import paper_2307_04688_gb300 as cb
+    from paper_2307_04688_gb300 import build as B
+    B.build()
+    ctx = cb.Context(0)
+    print(json.dumps(training_throughput(args, ctx)))
+    ctx.close()
+
+
 def run_paths(args):
     """Equilibrium time paths of the 3-player game at n = 17 (the +-30 % draw, seed 2):
     the FP64 solve to 1e-10 (not timed), then 4,096 paths of 2,000 steps from seeded
@@ -903,6 +973,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "paths":
         run_paths(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_ours(args)
 

@@ -90,14 +90,13 @@ def first_order_bounds(dims, p, X, T):
     return eY, gbound
 
 
-def _inputs(dims, regime, seed, count):
+def _inputs(dims, regime, seed, count, B=64):
     """Parameters, inputs and targets (FP32 values). 'mixed': N(0, 0.2^2) parameters, N(0, 1)
     inputs and targets (signs cancel in every sum, so the worst-case bounds are loose).
     'positive': weights in [0, 2/fan_in), biases in [-0.3, 0.3), inputs in [0.1, 1) and targets
     in [-3, -2) so that Y - T > 0: almost every term of every sum has one sign, the bounds are
     within ~10 % of each entry, and any wrong entry exceeds them."""
     rng = np.random.default_rng(seed)
-    B = 64
     if regime == "mixed":
         p = rng.standard_normal(count) * 0.2
         X = rng.standard_normal((B, dims[0]))
@@ -114,12 +113,20 @@ def _inputs(dims, regime, seed, count):
 
 
 @pytest.mark.parametrize("regime", ["positive", "mixed"])
-@pytest.mark.parametrize("dims", [[8, 32, 32, 20], [8, 256, 256, 300], [3, 16, 5], [8, 130, 130, 33]])
-def test_forward_and_gradient_entries_match_oracle(ctx, dims, regime):
+@pytest.mark.parametrize("dims,batch", [([8, 32, 32, 20], 64), ([8, 256, 256, 300], 64), ([3, 16, 5], 64),
+                                        ([8, 130, 130, 33], 64), ([8, 256, 1300], 200), ([5, 200, 200, 2100], 130),
+                                        ([8, 4992, 16], 256), ([8, 256, 4992], 256)])
+def test_forward_and_gradient_entries_match_oracle(ctx, dims, batch, regime):
     """Every output and every gradient entry within twice its first-order bound (the factor
-    covers second-order terms)."""
+    covers second-order terms). Batches of 200 and 130 leave a ragged K tile in the weight
+    gradients (K = batch) and a ragged row tile everywhere; outputs of 1,300 and 2,100 make the
+    hidden-layer gradient a long-K product with four or fewer output tiles, which is split
+    across CTAs and summed in a fixed order. A 4,992-wide hidden layer and a 4,992-wide
+    output layer at batch 256 give products with 78 output tiles, finished inside the GEMM
+    (GELU with both packed copies, the GELU derivative, the bias-only output and the wide
+    weight gradient)."""
     net = cb.Surrogate(ctx, dims[0], dims[1], len(dims) - 2, dims[-1], seed=1)
-    p, X, T = _inputs(dims, regime, sum(dims), net.param_count())
+    p, X, T = _inputs(dims, regime, sum(dims), net.param_count(), B=batch)
     net.set_params(p)
     B = X.shape[0]
     p64, X64, T64 = p.astype(np.float64), X.astype(np.float64), T.astype(np.float64)
