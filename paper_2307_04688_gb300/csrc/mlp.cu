@@ -453,13 +453,12 @@ __global__ void __launch_bounds__(kGemmThreads) splitk_reduce_kernel(const float
     finish_tile(stile, mt * kTM + r0, nt * kTN, kSlab, o);
 }
 
-// Packs an FP32 row-major matrix src (R x K, row stride ld) into the packed
-// forms that `o` asks for (o.M = R, o.N = K, o.epi = EPI_NONE, o.C = null).
-// Grid: (column tiles, row slabs).
-__global__ void __launch_bounds__(kGemmThreads) pack_kernel(const float *__restrict__ src, int64_t ld, const OutSpec o)
+// Packs the slab at rows m0 + [0, kSlab), columns n0 + [0, 128) of an FP32
+// row-major matrix src (R x K, row stride ld) into the packed forms that `o`
+// asks for (o.M = R, o.N = K, o.epi = EPI_NONE, o.C = null).
+__device__ __forceinline__ void pack_slab(float *stile, const float *__restrict__ src, int64_t ld, int m0, int n0,
+                                          const OutSpec &o)
 {
-    __shared__ __align__(16) float stile[kSlab * kLdT];
-    const int m0 = blockIdx.y * kSlab, n0 = blockIdx.x * kTN;
     float v[kSlab * kTN / kGemmThreads];
 #pragma unroll
     for (int u = 0; u < kSlab * kTN / kGemmThreads; ++u) {
@@ -476,14 +475,43 @@ __global__ void __launch_bounds__(kGemmThreads) pack_kernel(const float *__restr
     finish_tile(stile, m0, n0, kSlab, o);
 }
 
-// The mean-squared-error gradient dY = 2 (Y - T) / (B F) on one slab (Y, T
-// row-major B x F), the loss accumulated into *loss, and dY finished through
-// `o` (FP32 copy and the two packed forms for backpropagation).
 // Grid: (column tiles, row slabs).
-__global__ void __launch_bounds__(kGemmThreads) mse_tile_kernel(const float *__restrict__ Y, const float *__restrict__ T,
-                                                                float scale, float *__restrict__ loss, const OutSpec o)
+__global__ void __launch_bounds__(kGemmThreads) pack_kernel(const float *__restrict__ src, int64_t ld, const OutSpec o)
 {
     __shared__ __align__(16) float stile[kSlab * kLdT];
+    pack_slab(stile, src, ld, blockIdx.y * kSlab, blockIdx.x * kTN, o);
+}
+
+// One matrix of a multi-matrix pack: its blocks are first_block ..
+// first_block + col_tiles * slabs - 1 of the launch.
+struct PackJob {
+    const float *src;
+    int64_t ld;
+    OutSpec o;
+    int col_tiles, first_block;
+};
+
+// Packs every weight matrix of a network in one launch (1-D grid over the
+// jobs' blocks; a block finds its job by the jobs' first blocks).
+__global__ void __launch_bounds__(kGemmThreads) pack_multi_kernel(const PackJob *__restrict__ jobs, int njobs)
+{
+    __shared__ __align__(16) float stile[kSlab * kLdT];
+    int j = 0;
+    while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].first_block) ++j;
+    const PackJob jb = jobs[j];
+    const int local = (int)blockIdx.x - jb.first_block;
+    pack_slab(stile, jb.src, jb.ld, (local / jb.col_tiles) * kSlab, (local % jb.col_tiles) * kTN, jb.o);
+}
+
+// The mean-squared-error gradient dY = 2 (Y - T) / (B F) on one slab (Y, T
+// row-major B x F), the block's share of the loss into part[block] (summed in a
+// fixed order by loss_sum_kernel), and dY finished through `o` (FP32 copy and
+// the two packed forms for backpropagation). Grid: (column tiles, row slabs).
+__global__ void __launch_bounds__(kGemmThreads) mse_tile_kernel(const float *__restrict__ Y, const float *__restrict__ T,
+                                                                float scale, float *__restrict__ part, const OutSpec o)
+{
+    __shared__ __align__(16) float stile[kSlab * kLdT];
+    __shared__ float wsum[kGemmThreads / 32];
     const int m0 = blockIdx.y * kSlab, n0 = blockIdx.x * kTN;
     constexpr int kPer = kSlab * kTN / kGemmThreads;
     float y[kPer], t[kPer];
@@ -503,9 +531,29 @@ __global__ void __launch_bounds__(kGemmThreads) mse_tile_kernel(const float *__r
         stile[(q / kTN) * kLdT + q % kTN] = 2.0f * d * scale;
     }
     for (int s = 16; s > 0; s >>= 1) local += __shfl_xor_sync(0xffffffffu, local, s);
-    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, local);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kGemmThreads / 32; ++w) t += wsum[w];
+        part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
     finish_tile(stile, m0, n0, kSlab, o);
+}
+
+// *loss += sum of part[0 .. n) in a fixed order (one block).
+__global__ void __launch_bounds__(256) loss_sum_kernel(const float *__restrict__ part, int n, float *__restrict__ loss)
+{
+    __shared__ float red[256];
+    float t = 0.0f;
+    for (int i = threadIdx.x; i < n; i += 256) t += part[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss += red[0];
 }
 
 // Launch through cudaLaunchKernelEx (typed arguments, error returned as a status).
@@ -719,15 +767,25 @@ struct cheb_mlp {
     // packed BF16 weights: wk[l] rows = out, K = in (forward); wt[l] rows = in, K = out (backward)
     std::vector<uint8_t *> wk, wt;
     bool wpack_valid = false;        // the packed weights match w
+    PackJob *d_jobs = nullptr;       // the weight-packing jobs (device), one per layer
+    int pack_blocks = 0;
+    // a second stream for the weight and bias gradients (concurrent with the
+    // input-gradient chain), and the events that fork and join it
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t = nullptr, ev_w = nullptr;
+    bool wpack_pending = false;      // packing on the side stream; wait for ev_w before the first GEMM
     // normalisation (inputs and targets)
     float *x_mean = nullptr, *x_inv = nullptr, *x_std = nullptr;
     float *y_mean = nullptr, *y_inv = nullptr, *y_std = nullptr;
     bool normalised = false;
     // batch workspace (sized for ws_batch rows)
     int ws_batch = 0;
-    float *Z = nullptr, *dZ = nullptr, *dH = nullptr, *X = nullptr, *T = nullptr, *loss = nullptr;
+    // Z: pre-activations, dZ: their gradients, level l (1..L) at act_off(l) of each
+    float *Z = nullptr, *dZ = nullptr, *X = nullptr, *T = nullptr, *loss = nullptr;
     int *rows = nullptr;
-    float *split_ws = nullptr;       // split-K partial tiles (num_sms of them)
+    float *split_ws = nullptr;       // split-K partial tiles (num_sms of them), main stream
+    float *split_ws2 = nullptr;      // the same for the side stream
+    float *loss_part = nullptr;      // per-block loss sums of the loss kernel
     // packed activations per level l = 0..L: hk (rows = batch, K = width), ht (rows = width,
     // K = batch); packed pre-activation gradients dzk, dzt (levels 1..L), same two forms
     std::vector<uint8_t *> hk, ht, dzk, dzt;
@@ -740,7 +798,7 @@ void free_batch(cheb_mlp *net)
 {
     for (void *p : net->batch_bufs) cudaFree(p);
     net->batch_bufs.clear();
-    net->Z = net->dZ = net->dH = net->X = net->T = net->split_ws = nullptr;
+    net->Z = net->dZ = net->X = net->T = net->split_ws = net->split_ws2 = net->loss_part = nullptr;
     net->rows = nullptr;
     net->hk.assign(net->L + 1, nullptr);
     net->ht.assign(net->L + 1, nullptr);
@@ -753,9 +811,8 @@ cheb_status net_ws(cheb_ctx *ctx, cheb_mlp *net, int B)
 {
     if (B <= net->ws_batch) return CHEB_OK;
     free_batch(net);
-    int64_t act = 0, maxw = 0;
+    int64_t act = 0;
     for (int l = 1; l <= net->L; ++l) act += (int64_t)B * net->dims[l];
-    for (int l = 0; l <= net->L; ++l) maxw = std::max<int64_t>(maxw, net->dims[l]);
     bool ok = true;
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
@@ -768,12 +825,14 @@ cheb_status net_ws(cheb_ctx *ctx, cheb_mlp *net, int B)
         return p;
     };
     net->Z = static_cast<float *>(alloc(sizeof(float) * act));
-    net->dZ = static_cast<float *>(alloc(sizeof(float) * B * maxw));
-    net->dH = static_cast<float *>(alloc(sizeof(float) * B * maxw));
+    net->dZ = static_cast<float *>(alloc(sizeof(float) * act));
     net->X = static_cast<float *>(alloc(sizeof(float) * B * net->dims[0]));
     net->T = static_cast<float *>(alloc(sizeof(float) * B * net->dims[net->L]));
     net->rows = static_cast<int *>(alloc(sizeof(int) * B));
     net->split_ws = static_cast<float *>(alloc(sizeof(float) * kTM * kTN * (size_t)std::max(ctx->num_sms, 1)));
+    net->split_ws2 = static_cast<float *>(alloc(sizeof(float) * kTM * kTN * (size_t)std::max(ctx->num_sms, 1)));
+    net->loss_part = static_cast<float *>(
+        alloc(sizeof(float) * (size_t)cdiv(net->dims[net->L], kTN) * cdiv(B, kTK) * (kTK / kSlab)));
     for (int l = 0; l <= net->L; ++l) {
         net->hk[l] = static_cast<uint8_t *>(alloc(packed_bytes(B, net->dims[l])));
         net->ht[l] = static_cast<uint8_t *>(alloc(packed_bytes(net->dims[l], B)));
@@ -827,12 +886,28 @@ cheb_status pack(const float *src, int64_t ld, int R, int K, uint8_t *pk, uint8_
 
 cheb_status pack_weights(cheb_mlp *net, cudaStream_t st)
 {
-    for (int l = 0; l < net->L; ++l) {
-        const int ni = net->dims[l], no = net->dims[l + 1];
-        cheb_status r = pack(net->w + net->woff[l], ni, no, ni, net->wk[l], net->wt[l], st);
-        if (r) return r;
+    cheb_status r = set_kernel_attrs();
+    if (r) return r;
+    {
+        ProfScope prof("mlp_pack_weights", st);
+        if ((r = launch(pack_multi_kernel, dim3((unsigned)net->pack_blocks), dim3(kGemmThreads), 0, st,
+                        (const PackJob *)net->d_jobs, net->L)))
+            return r;
     }
     net->wpack_valid = true;
+    return CHEB_OK;
+}
+
+// pack the weights on the side stream; the first GEMM of the next forward pass
+// waits for them (ev_w)
+cheb_status fork_weight_pack(cheb_mlp *net, cudaStream_t st)
+{
+    CHEB_CUDA_TRY(cudaEventRecord(net->ev_fork, st));
+    CHEB_CUDA_TRY(cudaStreamWaitEvent(net->side, net->ev_fork, 0));
+    cheb_status r = pack_weights(net, net->side);
+    if (r) return r;
+    CHEB_CUDA_TRY(cudaEventRecord(net->ev_w, net->side));
+    net->wpack_pending = true;
     return CHEB_OK;
 }
 
@@ -841,8 +916,12 @@ cheb_status pack_weights(cheb_mlp *net, cudaStream_t st)
 cheb_status forward(cheb_ctx *ctx, cheb_mlp *net, int B, bool train, cudaStream_t st)
 {
     cheb_status r;
-    if (!net->wpack_valid && (r = pack_weights(net, st))) return r;
+    if (!net->wpack_valid && (r = fork_weight_pack(net, st))) return r;
     if ((r = pack(net->X, net->dims[0], B, net->dims[0], net->hk[0], train ? net->ht[0] : nullptr, st))) return r;
+    if (net->wpack_pending) {
+        CHEB_CUDA_TRY(cudaStreamWaitEvent(st, net->ev_w, 0));
+        net->wpack_pending = false;
+    }
     for (int l = 0; l < net->L; ++l) {
         const int ni = net->dims[l], no = net->dims[l + 1];
         const bool last = (l == net->L - 1);
@@ -871,44 +950,59 @@ cheb_status forward(cheb_ctx *ctx, cheb_mlp *net, int B, bool train, cudaStream_
 float *output(cheb_mlp *net, int B) { return net->Z + act_off(net, net->L, B); }
 
 // loss gradient of the last layer from the normalised targets in T: FP32 into
-// net->dZ and the packed forms of level L
+// level L of net->dZ and the packed forms of level L
 cheb_status loss_grad(cheb_mlp *net, int B, const float *T, float *loss, cudaStream_t st)
 {
     cheb_status r = set_kernel_attrs();
     if (r) return r;
     const int O = net->dims[net->L];
     OutSpec o = no_out(B, O);
-    o.C = net->dZ;
+    o.C = net->dZ + act_off(net, net->L, B);
     o.pk = net->dzk[net->L];
     o.pk_kt = cdiv(O, kTK);
     o.pt = net->dzt[net->L];
     o.pt_kt = cdiv(B, kTK);
-    ProfScope prof("mlp_loss_grad", st);
-    return launch(mse_tile_kernel, dim3((unsigned)cdiv(O, kTN), (unsigned)(cdiv(B, kTK) * (kTK / kSlab))),
-                      dim3(kGemmThreads), 0, st, (const float *)output(net, B), T, 1.0f / ((float)B * O), loss, o);
+    const dim3 grid((unsigned)cdiv(O, kTN), (unsigned)(cdiv(B, kTK) * (kTK / kSlab)));
+    {
+        ProfScope prof("mlp_loss_grad", st);
+        if ((r = launch(mse_tile_kernel, grid, dim3(kGemmThreads), 0, st, (const float *)output(net, B), T,
+                        1.0f / ((float)B * O), net->loss_part, o)))
+            return r;
+    }
+    // the loss itself is only reported: summed on the side stream (joined at the end of backward)
+    CHEB_CUDA_TRY(cudaEventRecord(net->ev_fork, st));
+    CHEB_CUDA_TRY(cudaStreamWaitEvent(net->side, net->ev_fork, 0));
+    return launch(loss_sum_kernel, dim3(1), dim3(256), 0, net->side, (const float *)net->loss_part,
+                  (int)(grid.x * grid.y), loss);
 }
 
-// backward pass from the level-L gradient (net->dZ and its packed forms) to net->grad
+// backward pass from the level-L gradient (FP32 and packed) to net->grad. The
+// input-gradient chain (dZ of level l from dZ of level l + 1) runs on `st`;
+// each layer's weight and bias gradients fork to the side stream as soon as
+// their inputs exist and join `st` at the end, so they overlap the chain.
 cheb_status backward(cheb_ctx *ctx, cheb_mlp *net, int B, cudaStream_t st)
 {
-    float *dZ = net->dZ, *dH = net->dH;
     cheb_status r;
     for (int l = net->L - 1; l >= 0; --l) {
         const int ni = net->dims[l], no = net->dims[l + 1];
+        const float *dZo = net->dZ + act_off(net, l + 1, B);
+        CHEB_CUDA_TRY(cudaEventRecord(net->ev_fork, st));
+        CHEB_CUDA_TRY(cudaStreamWaitEvent(net->side, net->ev_fork, 0));
         // dW_l[o, i] = sum_b dZ[b, o] in[b, i]
         OutSpec g = no_out(no, ni);
         g.C = net->grad + net->woff[l];
-        if ((r = gemm(ctx, net->dzt[l + 1], cdiv(B, kTK), net->ht[l], cdiv(B, kTK), B, g, net->split_ws, st))) return r;
+        if ((r = gemm(ctx, net->dzt[l + 1], cdiv(B, kTK), net->ht[l], cdiv(B, kTK), B, g, net->split_ws2, net->side)))
+            return r;
         {
-            ProfScope prof("mlp_bias_grad", st);
-            if ((r = launch(bias_grad_kernel, dim3((unsigned)cdiv(no, 32)), dim3(256), 0, st, (const float *)dZ, B,
-                                no, net->grad + net->boff[l])))
+            ProfScope prof("mlp_bias_grad", net->side);
+            if ((r = launch(bias_grad_kernel, dim3((unsigned)cdiv(no, 32)), dim3(256), 0, net->side, dZo, B, no,
+                            net->grad + net->boff[l])))
                 return r;
         }
         if (l > 0) {
             // dZ_{l-1}[b, i] = (sum_o dZ[b, o] W_l[o, i]) GELU'(Z_{l-1}[b, i])
             OutSpec h = no_out(B, ni);
-            h.C = dH;
+            h.C = net->dZ + act_off(net, l, B);
             h.aux = net->Z + act_off(net, l, B);
             h.epi = EPI_GELU_BWD;
             h.pk = net->dzk[l];
@@ -917,9 +1011,10 @@ cheb_status backward(cheb_ctx *ctx, cheb_mlp *net, int B, cudaStream_t st)
             h.pt_kt = cdiv(B, kTK);
             if ((r = gemm(ctx, net->dzk[l + 1], cdiv(no, kTK), net->wt[l], cdiv(no, kTK), no, h, net->split_ws, st)))
                 return r;
-            std::swap(dZ, dH);
         }
     }
+    CHEB_CUDA_TRY(cudaEventRecord(net->ev_join, net->side));
+    CHEB_CUDA_TRY(cudaStreamWaitEvent(st, net->ev_join, 0));
     return CHEB_OK;
 }
 
@@ -989,6 +1084,36 @@ CHEB_API cheb_status surrogate_create(cheb_ctx *ctx, int32_t n_in, int32_t width
         cudaMemset(net->wk[l], 0, packed_bytes(no, ni));
         cudaMemset(net->wt[l], 0, packed_bytes(ni, no));
     }
+    {
+        std::vector<PackJob> jobs(net->L);
+        int first = 0;
+        for (int l = 0; l < net->L; ++l) {
+            const int ni = net->dims[l], no = net->dims[l + 1];
+            PackJob &j = jobs[l];
+            std::memset(&j, 0, sizeof(j));
+            j.src = net->w + net->woff[l];
+            j.ld = ni;
+            j.o = no_out(no, ni);
+            j.o.pk = net->wk[l];
+            j.o.pk_kt = cdiv(ni, kTK);
+            j.o.pt = net->wt[l];
+            j.o.pt_kt = cdiv(no, kTK);
+            j.col_tiles = cdiv(ni, kTN);
+            j.first_block = first;
+            first += j.col_tiles * cdiv(no, kTK) * (kTK / kSlab);   // row slabs up to a multiple of 64 rows
+        }
+        net->pack_blocks = first;
+        if (cudaMalloc(&net->d_jobs, sizeof(PackJob) * net->L) ||
+            cudaMemcpy(net->d_jobs, jobs.data(), sizeof(PackJob) * net->L, cudaMemcpyHostToDevice) ||
+            cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking) ||
+            cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming) ||
+            cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming) ||
+            cudaEventCreateWithFlags(&net->ev_t, cudaEventDisableTiming) ||
+            cudaEventCreateWithFlags(&net->ev_w, cudaEventDisableTiming)) {
+            surrogate_destroy(net);
+            return fail(CHEB_ENOMEM, "surrogate allocation failed");
+        }
+    }
     free_batch(net);
     cudaMemcpy(net->w, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
     cudaMemset(net->m, 0, sizeof(float) * off);
@@ -1018,6 +1143,10 @@ CHEB_API cheb_status surrogate_destroy(cheb_mlp *net)
     for (uint8_t *p : net->wt)
         if (p) cudaFree(p);
     for (void *p : net->batch_bufs) cudaFree(p);
+    if (net->d_jobs) cudaFree(net->d_jobs);
+    if (net->side) cudaStreamDestroy(net->side);
+    for (cudaEvent_t e : {net->ev_fork, net->ev_join, net->ev_t, net->ev_w})
+        if (e) cudaEventDestroy(e);
     delete net;
     return CHEB_OK;
 }
@@ -1133,13 +1262,18 @@ CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double 
         net->wpack_valid = false;
         for (int64_t k = 0; k < steps; ++k) {
             const int *rows = d_perm + k * B;
-            if ((e = launch(gather_norm_kernel, dim3(blocks_for((int64_t)B * F)), dim3(256), 0, s, X, x_stride,
-                                rows, B, F, (const float *)net->x_mean, (const float *)net->x_inv, net->X)))
+            // the weights are packed and the targets gathered on the side stream,
+            // concurrently with the input gather and the start of the forward pass
+            if ((e = fork_weight_pack(net, s))) return e;
+            if ((e = launch(gather_norm_kernel, dim3(blocks_for((int64_t)B * O)), dim3(256), 0, net->side, Y, y_stride,
+                            rows, B, O, (const float *)net->y_mean, (const float *)net->y_inv, net->T)))
                 return e;
-            if ((e = launch(gather_norm_kernel, dim3(blocks_for((int64_t)B * O)), dim3(256), 0, s, Y, y_stride,
-                                rows, B, O, (const float *)net->y_mean, (const float *)net->y_inv, net->T)))
+            CHEB_CUDA_TRY(cudaEventRecord(net->ev_t, net->side));
+            if ((e = launch(gather_norm_kernel, dim3(blocks_for((int64_t)B * F)), dim3(256), 0, s, X, x_stride,
+                            rows, B, F, (const float *)net->x_mean, (const float *)net->x_inv, net->X)))
                 return e;
             if ((e = forward(ctx, net, B, true, s))) return e;
+            CHEB_CUDA_TRY(cudaStreamWaitEvent(s, net->ev_t, 0));
             if ((e = loss_grad(net, B, net->T, d_acc, s))) return e;
             if ((e = backward(ctx, net, B, s))) return e;
             if ((e = launch(adam_kernel, dim3(blocks_for(net->nparam)), dim3(256), 0, s, net->nparam, net->w,
