@@ -50,6 +50,7 @@ using namespace tc;
 constexpr int kTile = 128;
 constexpr int kThreads = 256;
 constexpr int kProducer = kTile;    // issues the bulk copies and the MMAs (first thread of the upper half)
+constexpr int kPairs = 32;          // (instance, player) pairs interleaved in the work order
 
 template <int FORM> struct GForm;
 template <> struct GForm<CHEB_BF16X3> {
@@ -360,11 +361,29 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const int half = tid >> 7;
     const int quarter = warp & 3, ehalf = warp >> 2;
 
+    // Work items are (instance q, player i, tile t). They are ordered in blocks
+    // of kPairs (q, i) pairs with the pair fastest inside a block, so the CTAs
+    // working at one time spread over kPairs coefficient tensors (each read by
+    // a few CTAs, all of them resident in L2) instead of all streaming the same
+    // one; a contiguous tile order made every CTA fetch the same bytes at once
+    // and the bulk copies of B waited on that contention.
+    const int npair = B * JJ;
+    auto decode = [&](int64_t it, int &t, int &i, int &q) {
+        const int64_t blk = it / ((int64_t)kPairs * tiles);
+        const int rem = (int)(it - blk * kPairs * tiles);
+        const int64_t left = npair - blk * kPairs;
+        const int pb = left < kPairs ? (int)left : kPairs;
+        t = rem / pb;
+        const int pair = (int)(blk * kPairs) + rem % pb;
+        i = pair % JJ;
+        q = pair / JJ;
+    };
     // the next work item at or after `from` whose instance is still iterating
     // in split precision (uniform across the block)
     auto next_item = [&](int64_t from) {
         for (int64_t it = from; it < items; it += gridDim.x) {
-            const int q = (int)(it / (tiles * JJ));
+            int t, i, q;
+            decode(it, t, i, q);
             if (!stats[q].done && stats[q].mode == 1) return it;
         }
         return items;
@@ -410,9 +429,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     // T_{k_a}(x_a(j)) is formed and split, T_{k_b}(x_b(j)) is staged for the
     // epilogue, and chunk 0's MMA is issued.
     auto prologue = [&](int64_t it) {
-        const int t = (int)(it % tiles);
-        const int i = (int)((it / tiles) % JJ);
-        const int q = (int)(it / (tiles * JJ));
+        int t, i, q;
+        decode(it, t, i, q);
         const GameDev &g = insts[q];
         int o[3] = {0, 0, 0};
         other_modes<JJ>(i, o);
@@ -477,9 +495,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     __syncthreads();
     tc_fence_after();
     while (item < items) {
-        const int t = (int)(item % tiles);
-        const int i = (int)((item / tiles) % JJ);
-        const int q = (int)(item / (tiles * JJ));
+        int t, i, q;
+        decode(item, t, i, q);
         GameStat *st = &stats[q];
         const GameDev &g = insts[q];
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
@@ -506,7 +523,6 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         for (int c = 0; c < S::NCH; ++c) {
             const int buf = c & 1;
             const int kis = (c == S::NCH - 1) ? NN - c * S::CHKI : S::CHKI;   // k_i in this chunk
-            if (tid == kProducer && c + 1 < S::NCH) issue_mma(c + 1);
             if (mbar_wait_bounded(&bars[2 + buf], (mma_phase >> buf) & 1u, err)) {
                 mma_phase ^= 1u << buf;
                 mma_out &= ~(1u << buf);
@@ -514,6 +530,11 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 *abort_flag = 1;
             }
             tc_fence_after();
+            // chunk c + 1 goes to the tensor cores as soon as chunk c is done (its
+            // accumulator was drained before the last barrier); issued earlier, the
+            // MMAs queue behind chunk c and hold the producer's warp back from
+            // its share of the epilogue
+            if (tid == kProducer && c + 1 < S::NCH) issue_mma(c + 1);
             // the B stage of chunk c is free again: prefetch chunk c + 2 into it
             // (not while a copy into it is still pending after a timeout)
             if (tid == kProducer && c + 2 < S::NCH && !(pending & (1u << buf))) {
