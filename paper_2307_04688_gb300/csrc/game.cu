@@ -78,69 +78,122 @@ __global__ void next_state_kernel(const GameDev *__restrict__ insts, const GameS
     }
 }
 
-// FP64 player update: one thread per (node, player). The series in the
-// player's own coordinate is w[k] = sum over the other modes of
-// C_i[..k..] prod_s T_{k_s}(x_s(j)), by nested contraction (last mode first).
+// FP64 player update. A block of 128 threads covers 32 nodes of one player
+// and splits the n coefficients k of each node's series over four k groups:
+// thread (node q = tid % 32, group kg = tid / 32) contracts
+// w[k] = sum over the other modes of C_i[..k..] prod_s T_{k_s}(x_s(j)) by
+// nested contraction (last mode first) for its share of k, four k at a time
+// (independent FMA chains, each w[k] summed in the same order as one k at a
+// time), so a single game gives four times as many warps to hide the FP64
+// latency. The Chebyshev rows of the 32 nodes sit in shared memory, w goes
+// through shared memory, and the first warp maximises over the controls.
+constexpr int kF64Nodes = 32;
 __global__ void __launch_bounds__(128)
 player_f64_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stats)
 {
+    extern __shared__ double f64_s[];   // T rows [J - 1][n][32], then w [n][32]
     const int inst = blockIdx.z, i = blockIdx.y;
-    const GameDev &gref = insts[inst];
+    const GameDev &g = insts[inst];
     GameStat *st = &stats[inst];
     if (st->done || st->mode != 0) return;
-    const GameDev g = gref;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.NP) return;
     const int J = g.J, n = g.n, NP = g.NP;
-    double T[4][kGameNMax];
-    for (int s = 0; s < J; ++s) {
-        if (s == i) continue;
-        const double x = g.X[s * NP + j];
-        T[s][0] = 1.0;
-        if (n > 1) T[s][1] = x;
-        for (int k = 2; k < n; ++k) T[s][k] = 2.0 * x * T[s][k - 1] - T[s][k - 2];
+    const int q = threadIdx.x % kF64Nodes, kg = threadIdx.x / kF64Nodes;
+    const int j = blockIdx.x * kF64Nodes + q;
+    const bool valid = j < NP;
+    double *T_s = f64_s;
+    double *w_s = f64_s + (size_t)(J - 1) * n * kF64Nodes;
+    auto T = [&](int slot, int k) -> double & { return T_s[(slot * n + k) * kF64Nodes + q]; };
+    // other mode of slot t (the modes other than i in increasing order)
+    auto other = [&](int t) { return t < i ? t : t + 1; };
+    auto stride = [&](int s) {
+        int v = 1;
+        for (int r = s + 1; r < J; ++r) v *= n;
+        return v;
+    };
+    // the rows of the node's other coordinates: group kg takes slots kg, kg + 4, ...
+    for (int t = kg; t < J - 1; t += 4) {
+        const double x = valid ? g.X[other(t) * NP + j] : 0.0;
+        double t0 = 1.0, t1 = x;
+        T(t, 0) = 1.0;
+        if (n > 1) T(t, 1) = x;
+        for (int k = 2; k < n; ++k) {
+            const double t2 = 2.0 * x * t1 - t0;
+            T(t, k) = t2;
+            t0 = t1;
+            t1 = t2;
+        }
     }
-    // strides of the modes in C_i (row-major)
-    int stride[4];
-    stride[J - 1] = 1;
-    for (int s = J - 2; s >= 0; --s) stride[s] = stride[s + 1] * n;
-    int other[3], no = 0;
-    for (int s = 0; s < J; ++s)
-        if (s != i) other[no++] = s;
+    __syncthreads();
+    const int no = J - 1;
     const double *C = g.C + (size_t)i * NP;
-    double w[kGameNMax];
-    for (int k = 0; k < n; ++k) {
-        const double *Ck = C + (size_t)k * stride[i];
-        double acc = 0.0;
+    const int si = stride(i);
+    const int kq = (n + 3) / 4;
+    const int klo = kg * kq, khi = klo + kq < n ? klo + kq : n;
+    for (int k0 = klo; valid && k0 < khi; k0 += 4) {
+        const int kb = khi - k0 < 4 ? khi - k0 : 4;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
         if (no == 0) {
-            acc = Ck[0];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < kb) acc[r] = C[(size_t)(k0 + r) * si];
         } else if (no == 1) {
-            const int s0 = other[0];
-            for (int a = 0; a < n; ++a) acc = fma(Ck[a * stride[s0]], T[s0][a], acc);
-        } else if (no == 2) {
-            const int s0 = other[0], s1 = other[1];
+            const int s0 = stride(other(0));
             for (int a = 0; a < n; ++a) {
-                double t = 0.0;
-                const double *Ca = Ck + a * stride[s0];
-                for (int b = 0; b < n; ++b) t = fma(Ca[b * stride[s1]], T[s1][b], t);
-                acc = fma(t, T[s0][a], acc);
+                const double ta = T(0, a);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < kb) acc[r] = fma(C[(size_t)(k0 + r) * si + a * s0], ta, acc[r]);
+            }
+        } else if (no == 2) {
+            const int s0 = stride(other(0)), s1 = stride(other(1));
+            for (int a = 0; a < n; ++a) {
+                double t[4] = {0.0, 0.0, 0.0, 0.0};
+                const double *Ca = C + (size_t)k0 * si + a * s0;
+                for (int b = 0; b < n; ++b) {
+                    const double tb = T(1, b);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r < kb) t[r] = fma(Ca[(size_t)r * si + b * s1], tb, t[r]);
+                }
+                const double ta = T(0, a);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < kb) acc[r] = fma(t[r], ta, acc[r]);
             }
         } else {
-            const int s0 = other[0], s1 = other[1], s2 = other[2];
+            const int s0 = stride(other(0)), s1 = stride(other(1)), s2 = stride(other(2));
             for (int a = 0; a < n; ++a) {
-                double ta = 0.0;
+                double ta[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int b = 0; b < n; ++b) {
-                    double t = 0.0;
-                    const double *Cab = Ck + a * stride[s0] + b * stride[s1];
-                    for (int c = 0; c < n; ++c) t = fma(Cab[c * stride[s2]], T[s2][c], t);
-                    ta = fma(t, T[s1][b], ta);
+                    double t[4] = {0.0, 0.0, 0.0, 0.0};
+                    const double *Cab = C + (size_t)k0 * si + a * s0 + b * s1;
+                    for (int c = 0; c < n; ++c) {
+                        const double tc = T(2, c);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            if (r < kb) t[r] = fma(Cab[(size_t)r * si + c * s2], tc, t[r]);
+                    }
+                    const double tb = T(1, b);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r < kb) ta[r] = fma(t[r], tb, ta[r]);
                 }
-                acc = fma(ta, T[s0][a], acc);
+                const double tA = T(0, a);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < kb) acc[r] = fma(ta[r], tA, acc[r]);
             }
         }
-        w[k] = acc;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r < kb) w_s[(k0 + r) * kF64Nodes + q] = acc[r];
     }
-    player_finish(g, st, i, j, w);
+    __syncthreads();
+    if (kg == 0 && valid) {
+        double w[kGameNMax];
+        for (int k = 0; k < n; ++k) w[k] = w_s[k * kF64Nodes + q];
+        player_finish(g, st, i, j, w);
+    }
 }
 
 // u, Vn <- u_new, Vn_new for instances still running (grid: node blocks x instances).
@@ -416,6 +469,19 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
 
     // ---- one iteration ----
     const unsigned node_blocks = (unsigned)((NP + 127) / 128);
+    // the FP64 player update: 32 nodes per block, their J - 1 Chebyshev rows and
+    // w in shared memory
+    const unsigned f64_blocks = (unsigned)((NP + kF64Nodes - 1) / kF64Nodes);
+    const size_t f64_smem = sizeof(double) * (size_t)J * (size_t)n * kF64Nodes;
+    {
+        static PerDevice attr;
+        cheb_status ra = per_device_once(attr, [](int *) -> cheb_status {
+            CHEB_CUDA_TRY(cudaFuncSetAttribute(player_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(double) * 4 * kGameNMax * kF64Nodes)));
+            return CHEB_OK;
+        }, nullptr);
+        if (ra) return ra;
+    }
     auto enqueue_iteration = [&](cudaStream_t s) -> cheb_status {
         cheb_status e;
         if (any_v0 || any_u0) {
@@ -439,7 +505,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
         }
         if (!general && (prec == CHEB_FP64 || (split && hinst[0].polish && hinst[0].polish_mode == 0))) {
             ProfScope prof("game_player_f64", s);
-            player_f64_kernel<<<dim3(node_blocks, J, B), 128, 0, s>>>(d_inst, d_stat);
+            player_f64_kernel<<<dim3(f64_blocks, J, B), 128, f64_smem, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
         if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, df_refit, s))) return e;
