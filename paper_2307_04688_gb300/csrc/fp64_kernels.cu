@@ -181,6 +181,36 @@ struct PointDims {
     double a[6], b[6];
 };
 
+// The Chebyshev rows of each thread's point live in shared memory as
+// [row][thread] (rows of mode s from sum_{r<s} n_r), conflict-free and with no
+// run-time indexed per-thread array. Returns the row offset of mode s.
+__device__ __forceinline__ int point_row_offset(const PointDims &D, int s)
+{
+    int o = 0;
+    for (int r = 0; r < s; ++r) o += D.n[r];
+    return o;
+}
+
+__device__ __forceinline__ void point_rows(const PointDims &D, int modes, const double *__restrict__ x, int64_t j,
+                                           double *Ts)
+{
+    const int nt = blockDim.x, tid = threadIdx.x;
+    int o = 0;
+    for (int s = 0; s < modes; ++s) {
+        const double xr = (2.0 * x[j * D.d + s] - (D.a[s] + D.b[s])) / (D.b[s] - D.a[s]);
+        double t0 = 1.0, t1 = xr;
+        Ts[o * nt + tid] = 1.0;
+        if (D.n[s] > 1) Ts[(o + 1) * nt + tid] = xr;
+        for (int l = 2; l < D.n[s]; ++l) {
+            const double t2 = 2.0 * xr * t1 - t0;
+            Ts[(o + l) * nt + tid] = t2;
+            t0 = t1;
+            t1 = t2;
+        }
+        o += D.n[s];
+    }
+}
+
 // One thread per point: T values per mode, then the nested contraction
 // sum_{l_1} T(x_1) ( sum_{l_2} T(x_2) ( ... sum_{l_d} c_l T(x_d) ) ) with the
 // innermost mode contiguous in memory. All threads of a warp read the same
@@ -188,33 +218,28 @@ struct PointDims {
 __global__ void eval_points_f64_kernel(PointDims D, const double *__restrict__ c, int64_t P,
                                        const double *__restrict__ x, double *__restrict__ out)
 {
+    extern __shared__ double Ts[];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P) return;
-    const int d = D.d;
-    double T[6 * kMaxN];
-    for (int s = 0; s < d; ++s) {
-        const double xr = (2.0 * x[j * d + s] - (D.a[s] + D.b[s])) / (D.b[s] - D.a[s]);
-        double *Ts = T + s * kMaxN;
-        Ts[0] = 1.0;
-        if (D.n[s] > 1) Ts[1] = xr;
-        for (int l = 2; l < D.n[s]; ++l) Ts[l] = 2.0 * xr * Ts[l - 1] - Ts[l - 2];
-    }
+    const int d = D.d, nt = blockDim.x, tid = threadIdx.x;
+    point_rows(D, d, x, j, Ts);
+    auto T = [&](int s, int l) { return Ts[(point_row_offset(D, s) + l) * nt + tid]; };
     int64_t outer = 1;
     for (int s = 0; s < d - 1; ++s) outer *= D.n[s];
     const int nl = D.n[d - 1];
-    const double *Tl = T + (d - 1) * kMaxN;
+    const double *Tl = Ts + (size_t)point_row_offset(D, d - 1) * nt + tid;
     double part[6] = {0, 0, 0, 0, 0, 0};
     int idx[6] = {0, 0, 0, 0, 0, 0};
     double result = 0.0;
     const double *cp = c;
     for (int64_t o = 0; o < outer; ++o) {
         double t = 0.0;
-        for (int k = 0; k < nl; ++k) t = fma(cp[k], Tl[k], t);
+        for (int k = 0; k < nl; ++k) t = fma(cp[k], Tl[(size_t)k * nt], t);
         cp += nl;
         int s = d - 2;
         double v = t;
         while (s >= 0) {
-            part[s] = fma(T[s * kMaxN + idx[s]], v, part[s]);
+            part[s] = fma(T(s, idx[s]), v, part[s]);
             if (++idx[s] < D.n[s]) break;
             idx[s] = 0;
             v = part[s];
@@ -233,38 +258,33 @@ __global__ void eval_points_f64_kernel(PointDims D, const double *__restrict__ c
 __global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y, int64_t P,
                                         const double *__restrict__ x, float *__restrict__ out)
 {
+    extern __shared__ double Ts[];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P) return;
-    const int d = D.d;
+    const int d = D.d, nt = blockDim.x, tid = threadIdx.x;
     const int dm = d - 1;               // modes still to contract
     if (dm == 0) {
         out[j] = Y[j];
         return;
     }
-    double T[5 * kMaxN];
-    for (int s = 0; s < dm; ++s) {
-        const double xr = (2.0 * x[j * d + s] - (D.a[s] + D.b[s])) / (D.b[s] - D.a[s]);
-        double *Ts = T + s * kMaxN;
-        Ts[0] = 1.0;
-        if (D.n[s] > 1) Ts[1] = xr;
-        for (int l = 2; l < D.n[s]; ++l) Ts[l] = 2.0 * xr * Ts[l - 1] - Ts[l - 2];
-    }
+    point_rows(D, dm, x, j, Ts);
+    auto T = [&](int s, int l) { return Ts[(point_row_offset(D, s) + l) * nt + tid]; };
     int64_t outer = 1;
     for (int s = 0; s < dm - 1; ++s) outer *= D.n[s];
     const int nl = D.n[dm - 1];
-    const double *Tl = T + (dm - 1) * kMaxN;
+    const double *Tl = Ts + (size_t)point_row_offset(D, dm - 1) * nt + tid;
     double part[6] = {0, 0, 0, 0, 0, 0};
     int idx[6] = {0, 0, 0, 0, 0, 0};
     double result = 0.0;
     const float *yp = Y + j;
     for (int64_t o = 0; o < outer; ++o) {
         double t = 0.0;
-        for (int k = 0; k < nl; ++k) t = fma((double)yp[(int64_t)k * P], Tl[k], t);
+        for (int k = 0; k < nl; ++k) t = fma((double)yp[(int64_t)k * P], Tl[(size_t)k * nt], t);
         yp += (int64_t)nl * P;
         int s = dm - 2;
         double v = t;
         while (s >= 0) {
-            part[s] = fma(T[s * kMaxN + idx[s]], v, part[s]);
+            part[s] = fma(T(s, idx[s]), v, part[s]);
             if (++idx[s] < D.n[s]) break;
             idx[s] = 0;
             v = part[s];
@@ -274,6 +294,31 @@ __global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y
         if (s < 0) result = v;
     }
     out[j] = (float)result;
+}
+
+// Threads per block of the point kernels and their shared memory: the rows of
+// `modes` modes for every thread, at most 96 KB (128 threads, fewer for long rows).
+inline int point_threads(const PointDims &D, int modes, size_t *smem)
+{
+    int rows = 0;
+    for (int s = 0; s < modes; ++s) rows += D.n[s];
+    int threads = 128;
+    while (threads > 32 && (size_t)threads * rows * sizeof(double) > 96 * 1024) threads /= 2;
+    *smem = (size_t)threads * rows * sizeof(double);
+    return threads;
+}
+
+cheb_status point_attrs()
+{
+    static PerDevice attr;
+    return per_device_once(attr, [](int *) -> cheb_status {
+        const int bytes = 32 * 6 * kMaxN * (int)sizeof(double);
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(eval_points_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           bytes));
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(rowwise_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           bytes));
+        return CHEB_OK;
+    }, nullptr);
 }
 
 template <int Q>
@@ -410,8 +455,11 @@ cheb_status eval_points_tc(cheb_ctx *ctx, int d, const int32_t *n, const double 
         D.a[s] = s < d ? a[s] : -1.0;
         D.b[s] = s < d ? b[s] : 1.0;
     }
+    if ((r = point_attrs())) return r;
+    size_t smem = 0;
+    const int threads = point_threads(D, d - 1, &smem);
     ProfScope prof("rowwise_contract", st);
-    rowwise_contract_kernel<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(D, Y, P, x, out);
+    rowwise_contract_kernel<<<(unsigned)((P + threads - 1) / threads), threads, smem, st>>>(D, Y, P, x, out);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
@@ -428,10 +476,13 @@ cheb_status eval_points_f64(int d, const int32_t *n, const double *coeffs, const
         D.a[s] = s < d ? a[s] : -1.0;
         D.b[s] = s < d ? b[s] : 1.0;
     }
-    const int threads = 128;
+    cheb_status r = point_attrs();
+    if (r) return r;
+    size_t smem = 0;
+    const int threads = point_threads(D, d, &smem);
     const int64_t blocks = (P + threads - 1) / threads;
     ProfScope prof("eval_points_f64", st);
-    eval_points_f64_kernel<<<(unsigned)blocks, threads, 0, st>>>(D, coeffs, P, x, out);
+    eval_points_f64_kernel<<<(unsigned)blocks, threads, smem, st>>>(D, coeffs, P, x, out);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }

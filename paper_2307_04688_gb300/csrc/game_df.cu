@@ -91,15 +91,6 @@ __device__ __forceinline__ void df_mac(dacc &acc, dfl a, dfl b)
 
 __device__ __forceinline__ dfl df_done(const dacc &a) { return df_norm(a.hi, a.lo); }
 
-// T_0..T_{n-1}(x) in double-float by the three-term recurrence (valid for any x)
-__device__ __forceinline__ void df_row(int n, double x, dfl *T)
-{
-    const dfl xf = df_of(x);
-    T[0] = {1.0f, 0.0f};
-    if (n > 1) T[1] = xf;
-    for (int k = 2; k < n; ++k) T[k] = df_add(df_scale(df_mul(xf, T[k - 1]), 2.0f), df_neg(T[k - 2]));
-}
-
 // The Bellman objective along the next states as a function of the player's
 // own control, W(u) = h (u (A - u/2) - phi pbar^2 / 2) + delta sum_m w_m T_m(x),
 // x = xc + slope u, in FP32 with its first two derivatives (the Newton search).
@@ -176,23 +167,34 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const int inst = blockIdx.z, i = blockIdx.y;
     GameStat *st = &stats[inst];
     if (st->done || st->mode != 2) return;
-    const GameDev g = insts[inst];
+    const GameDev &g = insts[inst];
     const int nl = threadIdx.x / kDfGroup, grp = threadIdx.x % kDfGroup;
     const int j = blockIdx.x * kDfNodes + nl;
     const int J = g.J, n = g.n, NP = g.NP;
     const bool valid = j < NP;
     const int jc = valid ? j : NP - 1;
-    int stride[4];
-    stride[J - 1] = 1;
-    for (int s = J - 2; s >= 0; --s) stride[s] = stride[s + 1] * n;
-    int other[3], no = 0;
-    for (int s = 0; s < J; ++s)
-        if (s != i) other[no++] = s;
-    // the node's T rows, one other mode per thread, shared by its eight threads
+    // mode strides of C_i (row-major) and the modes other than i, by arithmetic
+    // (no run-time indexed per-thread arrays)
+    auto stride = [&](int s) {
+        int v = 1;
+        for (int r = s + 1; r < J; ++r) v *= n;
+        return v;
+    };
+    auto other = [&](int t) { return t < i ? t : t + 1; };
+    const int no = J - 1;
+    // the node's T rows, one other mode per thread, shared by its eight threads,
+    // by the double-float recurrence straight into shared memory
     if (grp < no) {
-        dfl Tr[kGameNMax];
-        df_row(n, g.X[other[grp] * NP + jc], Tr);
-        for (int k = 0; k < n; ++k) T_sm[nl][grp][k] = make_float2(Tr[k].hi, Tr[k].lo);
+        const dfl xf = df_of(g.X[other(grp) * NP + jc]);
+        dfl t0 = {1.0f, 0.0f}, t1 = xf;
+        T_sm[nl][grp][0] = make_float2(1.0f, 0.0f);
+        if (n > 1) T_sm[nl][grp][1] = make_float2(xf.hi, xf.lo);
+        for (int k = 2; k < n; ++k) {
+            const dfl t2 = df_add(df_scale(df_mul(xf, t1), 2.0f), df_neg(t0));
+            T_sm[nl][grp][k] = make_float2(t2.hi, t2.lo);
+            t0 = t1;
+            t1 = t2;
+        }
     }
     __syncthreads();
     auto Tq = [&](int q, int a) {
@@ -205,20 +207,20 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         return dfl{v.x, v.y};
     };
     for (int k = grp; k < n; k += kDfGroup) {
-        const size_t ck = (size_t)k * stride[i];
+        const size_t ck = (size_t)k * stride(i);
         dfl wk;
         if (no == 0) {
             wk = coef(ck);
         } else if (no == 1) {
             dacc acc;
-            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride[other[0]]), Tq(0, a));
+            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride(other(0))), Tq(0, a));
             wk = df_done(acc);
         } else if (no == 2) {
             dacc acc;
             for (int a = 0; a < n; ++a) {
                 dacc t;
-                const size_t ca = ck + (size_t)a * stride[other[0]];
-                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride[other[1]]), Tq(1, b));
+                const size_t ca = ck + (size_t)a * stride(other(0));
+                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride(other(1))), Tq(1, b));
                 df_mac(acc, df_done(t), Tq(0, a));
             }
             wk = df_done(acc);
@@ -228,8 +230,8 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                 dacc ta;
                 for (int b = 0; b < n; ++b) {
                     dacc t;
-                    const size_t cab = ck + (size_t)a * stride[other[0]] + (size_t)b * stride[other[1]];
-                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride[other[2]]), Tq(2, c));
+                    const size_t cab = ck + (size_t)a * stride(other(0)) + (size_t)b * stride(other(1));
+                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride(other(2))), Tq(2, c));
                     df_mac(ta, df_done(t), Tq(1, b));
                 }
                 df_mac(acc, df_done(ta), Tq(0, a));
