@@ -206,40 +206,82 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const float2 v = __ldg(C + idx);
         return dfl{v.x, v.y};
     };
-    for (int k = grp; k < n; k += kDfGroup) {
-        const size_t ck = (size_t)k * stride(i);
-        dfl wk;
+    // thread grp takes k = grp, grp + 8, ...; three of them at a time as three
+    // independent chains (each w[k] summed in the same order as one at a time)
+    const int si = stride(i);
+    const int s0 = no > 0 ? stride(other(0)) : 0, s1 = no > 1 ? stride(other(1)) : 0,
+              s2 = no > 2 ? stride(other(2)) : 0;
+    for (int m0 = grp; m0 < n; m0 += 3 * kDfGroup) {
+        const int left = (n - m0 + kDfGroup - 1) / kDfGroup;
+        const int kb = left < 3 ? left : 3;
+        size_t ck[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ck[r] = (size_t)(m0 + r * kDfGroup) * si;
+        dfl wk[3];
         if (no == 0) {
-            wk = coef(ck);
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (r < kb) wk[r] = coef(ck[r]);
         } else if (no == 1) {
-            dacc acc;
-            for (int a = 0; a < n; ++a) df_mac(acc, coef(ck + (size_t)a * stride(other(0))), Tq(0, a));
-            wk = df_done(acc);
+            dacc acc[3];
+            for (int a = 0; a < n; ++a) {
+                const dfl ta = Tq(0, a);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (r < kb) df_mac(acc[r], coef(ck[r] + (size_t)a * s0), ta);
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wk[r] = df_done(acc[r]);
         } else if (no == 2) {
-            dacc acc;
+            dacc acc[3];
             for (int a = 0; a < n; ++a) {
-                dacc t;
-                const size_t ca = ck + (size_t)a * stride(other(0));
-                for (int b = 0; b < n; ++b) df_mac(t, coef(ca + (size_t)b * stride(other(1))), Tq(1, b));
-                df_mac(acc, df_done(t), Tq(0, a));
-            }
-            wk = df_done(acc);
-        } else {
-            dacc acc;
-            for (int a = 0; a < n; ++a) {
-                dacc ta;
+                dacc t[3];
                 for (int b = 0; b < n; ++b) {
-                    dacc t;
-                    const size_t cab = ck + (size_t)a * stride(other(0)) + (size_t)b * stride(other(1));
-                    for (int c = 0; c < n; ++c) df_mac(t, coef(cab + (size_t)c * stride(other(2))), Tq(2, c));
-                    df_mac(ta, df_done(t), Tq(1, b));
+                    const dfl tb = Tq(1, b);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        if (r < kb) df_mac(t[r], coef(ck[r] + (size_t)a * s0 + (size_t)b * s1), tb);
                 }
-                df_mac(acc, df_done(ta), Tq(0, a));
+                const dfl ta = Tq(0, a);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (r < kb) df_mac(acc[r], df_done(t[r]), ta);
             }
-            wk = df_done(acc);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wk[r] = df_done(acc[r]);
+        } else {
+            dacc acc[3];
+            for (int a = 0; a < n; ++a) {
+                dacc ta[3];
+                for (int b = 0; b < n; ++b) {
+                    dacc t[3];
+                    for (int c = 0; c < n; ++c) {
+                        const dfl tc = Tq(2, c);
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+                            if (r < kb)
+                                df_mac(t[r], coef(ck[r] + (size_t)a * s0 + (size_t)b * s1 + (size_t)c * s2), tc);
+                    }
+                    const dfl tb = Tq(1, b);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        if (r < kb) df_mac(ta[r], df_done(t[r]), tb);
+                }
+                const dfl tA = Tq(0, a);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (r < kb) df_mac(acc[r], df_done(ta[r]), tA);
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wk[r] = df_done(acc[r]);
         }
-        w_sm[nl][k] = make_float2(wk.hi, wk.lo);
-        wf_sm[nl][k] = wk.hi + wk.lo;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (r < kb) {
+                const int k = m0 + r * kDfGroup;
+                w_sm[nl][k] = make_float2(wk[r].hi, wk[r].lo);
+                wf_sm[nl][k] = wk[r].hi + wk[r].lo;
+            }
     }
     __syncwarp();       // a node's eight threads share a warp
     if (grp != 0 || !valid) return;
