@@ -139,6 +139,13 @@ struct SlabSkip {
 // Applied d times it takes each slab's tensor through all its modes and back
 // to their original order, slab by slab. Rows of skipped slabs are neither
 // computed nor written.
+// All J mode products of G slabs (each an n^J tensor, row-major) with the same
+// n x n matrix B in one launch, for small problems: one CTA per (slab, last
+// output index) keeps the intermediate tensors in shared memory. Bit-identical
+// to J successive modeprod_f64_slabs calls (same order of every sum). Returns
+// CHEB_EUNSUPPORTED (and launches nothing) when n^(J-1) > 4913.
+cheb_status modeprod_f64_chain(const double *X, const double *B, double *out, int64_t G, int J, int n,
+                               const SlabSkip &skip, cudaStream_t st);
 cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, int64_t G, int64_t R, int n, int m,
                                const SlabSkip &skip, cudaStream_t st);
 

@@ -104,6 +104,59 @@ __global__ void modeprod_f64_small_kernel(const double *__restrict__ X, const do
     out[t] = acc;
 }
 
+// All J mode products of a slab in one CTA per (slab g, last output index
+// k_J): the first product (the last mode, read from global memory) is taken
+// for this k_J only, and the other J - 1 products run on the resulting
+// n^(J-1) tensor in shared memory, each moving its new index to the front as
+// modeprod_f64_slabs does. Every output is the same sum in the same order as
+// in J successive slab products, so the results are bit-identical; the
+// intermediates never leave the SM and the J launches become one.
+constexpr int kChainMax = 4913;     // largest n^(J-1) held in shared memory
+constexpr int kChainThreads = 256;
+
+__global__ void __launch_bounds__(kChainThreads)
+modeprod_f64_chain_kernel(const double *__restrict__ X, const double *__restrict__ B, double *__restrict__ out,
+                          int J, int n, const SlabSkip sk)
+{
+    extern __shared__ double chain_s[];
+    const int kJ = blockIdx.x;
+    const int64_t g = blockIdx.y;
+    if (slab_skipped(sk, g)) return;
+    int R = 1;
+    for (int s = 0; s < J - 1; ++s) R *= n;
+    double *sB = chain_s;
+    double *cur = sB + n * n, *nxt = cur + R;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sB[t] = B[t];
+    __syncthreads();
+    // the last mode: cur[r] = sum_k B[k_J, k] X_g[r, k]
+    const double *Xg = X + g * (int64_t)R * n;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const double *xr = Xg + (int64_t)r * n;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc = fma(sB[kJ * n + k], __ldg(xr + k), acc);
+        cur[r] = acc;
+    }
+    __syncthreads();
+    // the other modes: view cur as [R / n rows x n], out[j (R / n) + r] = sum_k B[j, k] cur[r n + k]
+    const int Rp = R / n;
+    for (int step = 1; step < J; ++step) {
+        for (int t = threadIdx.x; t < n * Rp; t += blockDim.x) {
+            const int j = t / Rp, r = t - j * Rp;
+            const double *xr = cur + r * n;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(sB[j * n + k], xr[k], acc);
+            nxt[t] = acc;
+        }
+        __syncthreads();
+        double *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    // cur = C_g[k_1 .. k_{J-1}, k_J] for this k_J, (k_1 .. k_{J-1}) row-major
+    double *og = out + g * (int64_t)R * n;
+    for (int t = threadIdx.x; t < R; t += blockDim.x) og[(int64_t)t * n + kJ] = cur[t];
+}
+
 // T[j * n + l] = T_l(x~_j) by the three-term recurrence (valid off [-1,1]).
 __global__ void cheb_matrix_kernel(const double *__restrict__ x, int64_t stride, int64_t m, int n,
                                    double a, double b, double *__restrict__ T)
@@ -343,6 +396,28 @@ cheb_status modeprod_f64(const double *X, const double *B, double *out, int64_t 
                          cudaStream_t st)
 {
     return modeprod_f64_slabs(X, B, out, 1, R, n, m, SlabSkip{}, st);
+}
+
+cheb_status modeprod_f64_chain(const double *X, const double *B, double *out, int64_t G, int J, int n,
+                               const SlabSkip &skip, cudaStream_t st)
+{
+    int64_t R = 1;
+    for (int s = 0; s < J - 1; ++s) R *= n;
+    if (J < 1 || n < 1 || R > kChainMax || G > 65535) return CHEB_EUNSUPPORTED;
+    if (G <= 0) return CHEB_OK;
+    static PerDevice attr;
+    cheb_status r = per_device_once(attr, [](int *) -> cheb_status {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(modeprod_f64_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * (kMaxN * kMaxN + 2 * kChainMax))));
+        return CHEB_OK;
+    }, nullptr);
+    if (r) return r;
+    const size_t smem = sizeof(double) * ((size_t)n * n + 2 * (size_t)R);
+    ProfScope prof("modeprod_f64_chain J=" + std::to_string(J) + " n=" + std::to_string(n) + " G=" + std::to_string(G),
+                   st);
+    modeprod_f64_chain_kernel<<<dim3((unsigned)n, (unsigned)G), kChainThreads, smem, st>>>(X, B, out, J, n, skip);
+    CHEB_CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
 }
 
 cheb_status modeprod_f64_slabs(const double *X, const double *B, double *out, int64_t G, int64_t R, int n, int m,

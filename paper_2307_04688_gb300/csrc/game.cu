@@ -317,6 +317,11 @@ static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const
         sk.stride = (int64_t)(sizeof(GameStat) / sizeof(int));
         sk.per_flag = J;
     }
+    // small groups: all J products in one launch with the intermediates in shared memory
+    if (G * n <= 8 * ctx->num_sms) {
+        r = modeprod_f64_chain(Vn_new_all, M, C_all, G, J, n, sk, st);
+        if (r != CHEB_EUNSUPPORTED) return r;
+    }
     const double *src = Vn_new_all;
     double *bufs[2] = {tmp0, tmp1};
     for (int t = 0; t < J; ++t) {
