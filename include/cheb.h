@@ -292,6 +292,13 @@ CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, const doubl
  * current device. */
 CHEB_API cheb_status cheb_eval_grid_noalloc_status(void *stream);
 
+/* Bound, in SM cycles, of the device-side waits of cheb_eval_grid_noalloc
+ * (process-wide, all devices; default CHEB_WAIT_LIMIT_DEFAULT). A wait that
+ * runs out makes its kernel drain the copies and MMAs in flight and return;
+ * cheb_eval_grid_noalloc_status then reports CHEB_ETIMEOUT. Takes effect for
+ * calls made after it returns. Returns CHEB_EINVAL for a negative bound. */
+CHEB_API cheb_status cheb_eval_grid_noalloc_set_wait_limit(int64_t cycles);
+
 /* ------------------------------------------------------------------------
  * The J-player pollution game (Section 2, linear-quadratic specification,
  * time step h, Section 2.1):

@@ -23,6 +23,7 @@
 // overlap on the GPU (different streams, or different host threads) race on
 // the array and corrupt each other's results: serialise them.
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -36,6 +37,8 @@ constexpr size_t kTmatBytes = 1ull << 20;       // FP64 T matrices
 constexpr size_t kTotalBytes = kScratchBytes + kTmatBytes + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kTotalBytes];
+// bound, in SM cycles, of the device-side waits of this entry point (process-wide)
+static std::atomic<long long> g_noalloc_wait_limit{kDefaultWaitCycles};
 
 struct DeviceSlot {
     bool ready = false;
@@ -146,11 +149,20 @@ extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, 
                 reinterpret_cast<uintptr_t>(reinterpret_cast<float *>(base + kScratchBytes) - sizes[t]) &
                 ~uintptr_t(15));
         const int64_t R = cur / n[mode];
-        if ((st = modeprod_tc_raw(src, t == 0, Ts[mode], dst, R, n[mode], m[mode], prec, err, slot->num_sms, sm)))
+        if ((st = modeprod_tc_raw(src, t == 0, Ts[mode], dst, R, n[mode], m[mode], prec, err, slot->num_sms, sm,
+                                  nullptr, -1.0, 1.0, g_noalloc_wait_limit.load())))
             return st;
         cur = R * m[mode];
         src = dst;
     }
+    return CHEB_OK;
+}
+
+extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc_set_wait_limit(int64_t cycles)
+{
+    tl_ctx = nullptr;
+    if (cycles < 0) return fail(CHEB_EINVAL, "cheb_eval_grid_noalloc_set_wait_limit: cycles must be >= 0");
+    g_noalloc_wait_limit.store(cycles);
     return CHEB_OK;
 }
 

@@ -43,6 +43,8 @@ def lib():
     L.cheb_eval_grid_noalloc.restype = C.c_int
     L.cheb_eval_grid_noalloc_status.argtypes = [vp]
     L.cheb_eval_grid_noalloc_status.restype = C.c_int
+    L.cheb_eval_grid_noalloc_set_wait_limit.argtypes = [C.c_int64]
+    L.cheb_eval_grid_noalloc_set_wait_limit.restype = C.c_int
     import oracle as O
     O.build()
     return L
@@ -117,3 +119,33 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(lib):
     assert b"maximum" in lib.cheb_last_error()
     st = _noalloc(lib, c[:2, :2, :2, :2].contiguous(), xs, cb.precision("fp64"), out)
     assert st == 1
+
+
+def test_noalloc_reports_a_wait_that_ran_out(lib):
+    """With a wait bound of 0 cycles every device-side wait gives up at once: the kernels
+    drain their copies and MMAs with the full bound and return, and the status call reports
+    CHEB_ETIMEOUT (6). With the default bound restored the next call is correct again. A
+    negative bound is rejected."""
+    import oracle as O
+    import paper_2307_04688_gb300 as cb
+    from paper_2307_04688_gb300 import _lib
+    prec = cb.precision("bf16x6")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(9)
+    cn = rng.standard_normal((17, 17, 9))
+    xn = [rng.uniform(-1, 1, k) for k in (64, 40, 33)]
+    c = torch.from_numpy(cn).cuda()
+    xs = [torch.from_numpy(x).cuda() for x in xn]
+    out = torch.zeros((64, 40, 33), dtype=torch.float32, device="cuda")
+    assert lib.cheb_eval_grid_noalloc_set_wait_limit(-1) != 0
+    try:
+        assert lib.cheb_eval_grid_noalloc_set_wait_limit(0) == 0
+        assert _noalloc(lib, c, xs, prec, out) == 0, lib.cheb_last_error()
+        assert lib.cheb_eval_grid_noalloc_status(stream) == 6
+    finally:
+        assert lib.cheb_eval_grid_noalloc_set_wait_limit(_lib.CHEB_WAIT_LIMIT_DEFAULT) == 0
+    assert _noalloc(lib, c, xs, prec, out) == 0, lib.cheb_last_error()
+    assert lib.cheb_eval_grid_noalloc_status(stream) == 0, lib.cheb_last_error()
+    orc = O.eval_grid(cn, xn)
+    err = float(np.abs(out.double().cpu().numpy() - orc).max() / np.abs(orc).max())
+    assert err <= _bound("bf16x6", cn, xn, orc), err
