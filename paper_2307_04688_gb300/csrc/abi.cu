@@ -30,14 +30,19 @@ ProfScope::ProfScope(std::string nm, cudaStream_t s) : ctx(tl_ctx), name(std::mo
     if (ctx && ctx->prof_on) {
         a = prof_event(ctx);
         b = prof_event(ctx);
-        cudaEventRecord(a, st);
+        // inside a stream capture the pair becomes two event-record nodes of the
+        // graph, so the kernel is timed where the graph runs it
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            record_flags = cudaEventRecordExternal;
+        cudaEventRecordWithFlags(a, st, record_flags);
     }
 }
 
 ProfScope::~ProfScope()
 {
     if (a) {
-        cudaEventRecord(b, st);
+        cudaEventRecordWithFlags(b, st, record_flags);
         ctx->prof_pending.push_back({name, a, b});
     }
 }

@@ -75,6 +75,7 @@ struct ProfScope {
     std::string name;
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
+    unsigned record_flags = 0;   // cudaEventRecordExternal while `st` is being captured into a graph
     ProfScope(std::string nm, cudaStream_t s);
     ~ProfScope();
 };

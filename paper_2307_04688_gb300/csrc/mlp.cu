@@ -1284,9 +1284,11 @@ CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double 
         }
         return CHEB_OK;
     };
-    // one epoch is captured once into a CUDA graph (unless kernels are being timed)
+    // one epoch is captured once into a CUDA graph; with kernel timing on, the
+    // timing events are captured as event-record nodes, so each kernel is timed
+    // where it runs, inside the graph (the last replay's times are read)
     cudaGraphExec_t exec = nullptr;
-    if (!ctx->prof_on) {
+    {
         cudaStream_t cs = nullptr;
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
