@@ -194,6 +194,32 @@ def test_training_reduces_loss(ctx):
     net.close()
 
 
+def test_training_is_deterministic_and_timed_inside_the_graph(ctx):
+    """Training runs as CUDA graphs with the weight and bias gradients on a second stream; the
+    split-K partials and the loss are summed in a fixed order, so two runs from the same
+    parameters and seed give bit-identical weights and losses. With kernel timing on, the
+    timing events are captured into the graph and every kernel reports a positive time."""
+    rng = np.random.default_rng(6)
+    S, F, Ov = 2048, 8, 300
+    X = torch.from_numpy(rng.uniform(-1, 1, (S, F))).cuda()
+    Y = torch.from_numpy(rng.standard_normal((S, Ov))).cuda()
+    runs = []
+    for timed in (False, True):
+        net = cb.Surrogate(ctx, F, 256, 2, Ov, seed=11)
+        ctx.profile(timed)
+        losses = net.train(X, Y, epochs=3, batch=256, lr=1e-3, seed=5)
+        torch.cuda.synchronize()
+        if timed:
+            prof = ctx.profile_read()
+            ctx.profile(False)
+            gemms = {k: v for k, v in prof.items() if k.startswith("mlp_gemm")}
+            assert gemms and all(n > 0 and ms > 0 for n, ms in gemms.values()), prof
+        runs.append((net.get_params(), losses))
+        net.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+
+
 def test_warm_start_saves_iterations_small_games(ctx):
     """Train on method-generated solves (n = 5, FP64): nodal values and controls of one
     player per network; warm-start held-out games from the predictions."""
