@@ -45,7 +45,8 @@ typedef enum {
     CHEB_ENOCONV = 4,       /* game: max_iter reached before the tolerance */
     CHEB_ESTALL = 5,        /* game: residual stopped decreasing above the tolerance */
     CHEB_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
-    CHEB_EUNSUPPORTED = 7   /* valid request outside the implemented shapes */
+    CHEB_EUNSUPPORTED = 7,  /* valid request outside the implemented shapes */
+    CHEB_EBOUNDS = 8        /* checked build only: a device bounds check failed */
 } cheb_status;
 
 /* Arithmetic of the mode products.
@@ -87,13 +88,28 @@ CHEB_API cheb_status cheb_destroy(cheb_ctx *ctx);
  * string stays valid until the next call on the same thread. */
 CHEB_API const char *cheb_last_error(void);
 
-/* Library version as "major.minor.patch". */
+/* Library version as "major.minor.patch"; the checked build (below) appends
+ * "+check". */
 CHEB_API const char *cheb_version(void);
 
 /* Wait for all work on the context's device, then report and clear the
  * device error word that bounded device-side waits write when they run out
- * (CHEB_ETIMEOUT). Returns CHEB_OK if no kernel reported a failure. */
+ * (CHEB_ETIMEOUT). In the checked build it then reads and clears the bounds
+ * check words and returns CHEB_EBOUNDS, with the source file and line of the
+ * first failed check in cheb_last_error(), if any check failed. Returns
+ * CHEB_OK if no kernel reported a failure. */
 CHEB_API cheb_status cheb_device_status(cheb_ctx *ctx);
+
+/* The checked build. libcheb_check.so is the same library compiled with
+ * -DCHEB_CHECK: its kernels test the indexes and shared-memory offsets they
+ * compute against the extents of the buffers they address, record a failed
+ * test (its source line) in a device word and skip that access instead of
+ * trapping, and cheb_device_status reports it as CHEB_EBOUNDS. It exists to
+ * find indexing faults while developing; the default build compiles no check.
+ * cheb_check_selftest (checked build only; the default build does not export
+ * it) launches one kernel on the context's device that fails one check
+ * without touching memory, so that a caller can see the report path work. */
+CHEB_API cheb_status cheb_check_selftest(cheb_ctx *ctx);
 
 /* Bound of the device-side waits of the tensor-core grid evaluation
  * (cheb_eval_grid and cheb_eval_points in a split form): a CTA that has waited
@@ -286,7 +302,8 @@ CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, const doubl
 /* Device status of the last cheb_eval_grid_noalloc call on the current device:
  * waits for `stream` (the stream of that call), reads the error word of the
  * library's fixed array and returns CHEB_OK, or CHEB_ETIMEOUT if a bounded
- * device wait of that call ran out (its output is then undefined). The word is
+ * device wait of that call ran out (its output is then undefined); the checked
+ * build then reports failed bounds checks as cheb_device_status does. The word is
  * cleared by the next cheb_eval_grid_noalloc call, not by this one. Allocates
  * nothing; returns CHEB_EINVAL if cheb_eval_grid_noalloc never ran on the
  * current device. */

@@ -67,6 +67,14 @@ class Context:
     def device_status(self) -> None:
         check(load().cheb_device_status(self._h))
 
+    def check_selftest(self) -> None:
+        """Checked build only (CHEB_LIBRARY=check): launch one kernel that fails a
+        bounds check without touching memory; device_status() then raises CHEB_EBOUNDS."""
+        L = load()
+        if not hasattr(L, "cheb_check_selftest"):
+            raise RuntimeError("cheb_check_selftest needs the checked build (CHEB_LIBRARY=check)")
+        check(L.cheb_check_selftest(self._h))
+
     def profile(self, enable: bool) -> None:
         """Turn per-kernel CUDA-event timing on or off (clears the totals)."""
         check(load().cheb_profile(self._h, int(bool(enable))))

@@ -11,11 +11,14 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcheb.so")
+# the checked build (device bounds checks, CHEB_EBOUNDS), chosen for a process
+# by CHEB_LIBRARY=check before the first load()
+LIB_CHECK_PATH = os.path.join(HERE, "libcheb_check.so")
 
 CHEB_OK, CHEB_EINVAL, CHEB_ENOMEM, CHEB_ECUDA, CHEB_ENOCONV, CHEB_ESTALL, CHEB_ETIMEOUT, \
-    CHEB_EUNSUPPORTED = range(8)
+    CHEB_EUNSUPPORTED, CHEB_EBOUNDS = range(9)
 STATUS_NAMES = {0: "CHEB_OK", 1: "CHEB_EINVAL", 2: "CHEB_ENOMEM", 3: "CHEB_ECUDA", 4: "CHEB_ENOCONV",
-                5: "CHEB_ESTALL", 6: "CHEB_ETIMEOUT", 7: "CHEB_EUNSUPPORTED"}
+                5: "CHEB_ESTALL", 6: "CHEB_ETIMEOUT", 7: "CHEB_EUNSUPPORTED", 8: "CHEB_EBOUNDS"}
 CHEB_FP64, CHEB_TF32X3, CHEB_BF16X3, CHEB_BF16X6 = range(4)
 CHEB_DF64 = 4
 CHEB_WAIT_LIMIT_DEFAULT = 1 << 32
@@ -50,14 +53,23 @@ class GameResult(C.Structure):
 _lib = None
 
 
+def library_path() -> str:
+    """libcheb.so, or libcheb_check.so when CHEB_LIBRARY=check."""
+    v = os.environ.get("CHEB_LIBRARY", "")
+    if v not in ("", "default", "check"):
+        raise RuntimeError(f"CHEB_LIBRARY must be 'check' or unset, not {v!r}")
+    return LIB_CHECK_PATH if v == "check" else LIB_PATH
+
+
 def load():
     """Load libcheb.so (built by __graft_entry__.build()); raise if absent."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libcheb.so not found at {LIB_PATH}; run __graft_entry__.build() first")
-    L = C.CDLL(LIB_PATH)
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run __graft_entry__.build() first")
+    L = C.CDLL(path)
     vp, ip = C.c_void_p, C.POINTER(C.c_int32)
     dp = C.POINTER(C.c_double)
     L.cheb_create.argtypes = [C.POINTER(vp), C.c_int]
@@ -97,6 +109,9 @@ def load():
               "cheb_tuning_report", "cheb_create", "cheb_destroy", "cheb_device_status", "cheb_fit", "cheb_eval_grid", "cheb_eval_grid_host",
               "cheb_eval_points", "game_solve", "game_paths"):
         getattr(L, f).restype = C.c_int
+    if hasattr(L, "cheb_check_selftest"):      # the checked build only
+        L.cheb_check_selftest.argtypes = [vp]
+        L.cheb_check_selftest.restype = C.c_int
     _lib = L
     return L
 

@@ -62,6 +62,57 @@ static void prof_drain(cheb_ctx *c)
     c->prof_pending.clear();
 }
 
+#ifdef CHEB_CHECK
+namespace dcheck {
+namespace {
+struct ReaderEntry {
+    const char *file;
+    Reader read;
+};
+std::mutex &registry_mutex()
+{
+    static std::mutex mu;
+    return mu;
+}
+std::vector<ReaderEntry> &registry()
+{
+    static std::vector<ReaderEntry> r;
+    return r;
+}
+}  // namespace
+
+void register_reader(const char *file, Reader r)
+{
+    std::lock_guard<std::mutex> lock(registry_mutex());
+    registry().push_back({file, r});
+}
+
+// Reads and clears every translation unit's check word on the current device;
+// the first failure found (in registration order) is reported.
+cheb_status report()
+{
+    std::lock_guard<std::mutex> lock(registry_mutex());
+    std::string where;
+    for (const ReaderEntry &e : registry()) {
+        int line = 0;
+        const int ce = e.read(&line);
+        if (ce != 0) return cuda_fail((cudaError_t)ce, "reading a bounds check word");
+        if (line != 0 && where.empty()) where = std::string(e.file) + ":" + std::to_string(line);
+    }
+    if (!where.empty()) return fail(CHEB_EBOUNDS, "device bounds check failed at " + where);
+    return CHEB_OK;
+}
+
+namespace {
+__global__ void selftest_kernel(int flag)
+{
+    // fails when flag == 0 (always, as launched); touches no memory
+    if (!CHEB_DCHECK(flag != 0)) return;
+}
+}  // namespace
+}  // namespace dcheck
+#endif
+
 cheb_status fail(cheb_status st, const std::string &msg)
 {
     g_last_error = msg;
@@ -204,10 +255,15 @@ extern "C" {
 
 const char *cheb_last_error(void) { return g_last_error.c_str(); }
 
+#ifdef CHEB_CHECK
+const char *cheb_version(void) { return "0.1.0+check"; }
+#else
 const char *cheb_version(void) { return "0.1.0"; }
+#endif
 
 cheb_status cheb_create(cheb_ctx **ctx, int device)
 {
+    NvtxRange nvtx_range("cheb_create");
     if (!ctx) return fail(CHEB_EINVAL, "null ctx pointer");
     *ctx = nullptr;
     int count = 0;
@@ -232,6 +288,7 @@ cheb_status cheb_create(cheb_ctx **ctx, int device)
 
 cheb_status cheb_destroy(cheb_ctx *ctx)
 {
+    NvtxRange nvtx_range("cheb_destroy");
     if (!ctx) return CHEB_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
@@ -264,10 +321,29 @@ cheb_status cheb_device_status(cheb_ctx *ctx)
     CHEB_CUDA_TRY(cudaMemcpy(&v, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (v != 0) {
         CHEB_CUDA_TRY(cudaMemset(ctx->d_error, 0, sizeof(int)));
+#ifdef CHEB_CHECK
+        (void)dcheck::report();
+#endif
         return fail((cheb_status)v, "a device-side wait ran out of time");
     }
+#ifdef CHEB_CHECK
+    return dcheck::report();
+#else
+    return CHEB_OK;
+#endif
+}
+
+#ifdef CHEB_CHECK
+cheb_status cheb_check_selftest(cheb_ctx *ctx)
+{
+    NvtxRange nvtx_range("cheb_check_selftest");
+    cheb_status st = check_ctx(ctx);
+    if (st) return st;
+    dcheck::selftest_kernel<<<1, 1>>>(0);
+    CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
+#endif
 
 cheb_status cheb_set_wait_limit(cheb_ctx *ctx, int64_t cycles)
 {
@@ -338,6 +414,7 @@ cheb_status cheb_tuning_report(cheb_ctx *ctx, char *buf, int64_t buf_len)
 cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *values, double *coeffs,
                      void *stream)
 {
+    NvtxRange nvtx_range("cheb_fit");
     cheb_status st = check_ctx(ctx);
     if (st) return st;
     int64_t total = 0;
@@ -368,6 +445,7 @@ cheb_status cheb_fit(cheb_ctx *ctx, int d, const int32_t *n, const double *value
 cheb_status cheb_filter(cheb_ctx *ctx, int d, const int32_t *n, double *coeffs, double alpha, int32_t order,
                         void *stream)
 {
+    NvtxRange nvtx_range("cheb_filter");
     cheb_status st = check_ctx(ctx);
     if (st) return st;
     int64_t total = 0;
@@ -380,6 +458,7 @@ cheb_status cheb_filter(cheb_ctx *ctx, int d, const int32_t *n, double *coeffs, 
 cheb_status cheb_smooth(cheb_ctx *ctx, int d, const int32_t *n, double *values, double alpha, int32_t order,
                         void *stream)
 {
+    NvtxRange nvtx_range("cheb_smooth");
     cheb_status st = cheb_fit(ctx, d, n, values, values, stream);
     if (st) return st;
     if ((st = cheb_filter(ctx, d, n, values, alpha, order, stream))) return st;
@@ -409,6 +488,7 @@ cheb_status cheb_eval_grid(cheb_ctx *ctx, int d, const int32_t *n, const double 
                            const double *a, const double *b, const int32_t *m,
                            const double *const *x, void *out, cheb_precision prec, void *stream)
 {
+    NvtxRange nvtx_range("cheb_eval_grid");
     cheb_status st = check_ctx(ctx);
     if (st) return st;
     int64_t total = 0;
@@ -479,6 +559,7 @@ cheb_status cheb_eval_grid_host(cheb_ctx *ctx, int d, const int32_t *n, const do
                                 const double *a, const double *b, const int32_t *m,
                                 const double *const *x, void *out, cheb_precision prec, void *stream)
 {
+    NvtxRange nvtx_range("cheb_eval_grid_host");
     cheb_status st = check_ctx(ctx);
     if (st) return st;
     int64_t total = 0;
@@ -552,6 +633,7 @@ cheb_status cheb_eval_points(cheb_ctx *ctx, int d, const int32_t *n, const doubl
                              const double *a, const double *b, int64_t P, const double *x,
                              void *out, cheb_precision prec, void *stream)
 {
+    NvtxRange nvtx_range("cheb_eval_points");
     cheb_status st = check_ctx(ctx);
     if (st) return st;
     int64_t total = 0;

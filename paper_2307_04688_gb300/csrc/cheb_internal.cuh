@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cheb.h"
+#include "dcheck.cuh"
 
 namespace cheb {
 

@@ -42,6 +42,8 @@ modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
     const int64_t r0 = (int64_t)blockIdx.x * kF64Rows;
     const int j0 = blockIdx.y * kCols;
     const int rows = (int)((total - r0) < kF64Rows ? (total - r0) : kF64Rows);
+    // the staged rows and columns fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK((size_t)(kF64Rows * ns + kCols * n) * sizeof(double) <= dyn_smem_bytes() && r0 < total)) return;
     if (sk.flags) {
         bool any = false;
         for (int64_t g = r0 / R; g <= (r0 + rows - 1) / R; ++g) any = any || !slab_skipped(sk, g);
@@ -78,7 +80,7 @@ modeprod_f64_kernel(const double *__restrict__ X, const double *__restrict__ B,
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int j = j0 + tj + 4 * q;
-                if (j < m) og[(int64_t)j * R] = acc[q];
+                if (j < m && CHEB_DCHECK(g < G)) og[(int64_t)j * R] = acc[q];
             }
         }
     }
@@ -126,6 +128,8 @@ modeprod_f64_chain_kernel(const double *__restrict__ X, const double *__restrict
     for (int s = 0; s < J - 1; ++s) R *= n;
     double *sB = chain_s;
     double *cur = sB + n * n, *nxt = cur + R;
+    // B and the two intermediates fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK((size_t)(n * n + 2 * R) * sizeof(double) <= dyn_smem_bytes() && kJ < n)) return;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sB[t] = B[t];
     __syncthreads();
     // the last mode: cur[r] = sum_k B[k_J, k] X_g[r, k]
@@ -275,6 +279,8 @@ __global__ void eval_points_f64_kernel(PointDims D, const double *__restrict__ c
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P) return;
     const int d = D.d, nt = blockDim.x, tid = threadIdx.x;
+    // this thread's Chebyshev rows fit the dynamic shared memory
+    if (!CHEB_DCHECK((size_t)point_row_offset(D, d) * nt * sizeof(double) <= dyn_smem_bytes())) return;
     point_rows(D, d, x, j, Ts);
     auto T = [&](int s, int l) { return Ts[(point_row_offset(D, s) + l) * nt + tid]; };
     int64_t outer = 1;
@@ -320,6 +326,7 @@ __global__ void rowwise_contract_kernel(PointDims D, const float *__restrict__ Y
         out[j] = Y[j];
         return;
     }
+    if (!CHEB_DCHECK((size_t)point_row_offset(D, dm) * nt * sizeof(double) <= dyn_smem_bytes())) return;
     point_rows(D, dm, x, j, Ts);
     auto T = [&](int s, int l) { return Ts[(point_row_offset(D, s) + l) * nt + tid]; };
     int64_t outer = 1;

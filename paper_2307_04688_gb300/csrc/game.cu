@@ -97,6 +97,8 @@ player_f64_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ stat
     GameStat *st = &stats[inst];
     if (st->done || st->mode != 0) return;
     const int J = g.J, n = g.n, NP = g.NP;
+    // the J - 1 row blocks and w fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK((size_t)J * n * kF64Nodes * sizeof(double) <= dyn_smem_bytes())) return;
     const int q = threadIdx.x % kF64Nodes, kg = threadIdx.x / kF64Nodes;
     const int j = blockIdx.x * kF64Nodes + q;
     const bool valid = j < NP;
@@ -643,6 +645,7 @@ using namespace cheb::game;
 extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const cheb_game_params *params,
                                            const cheb_game_opts *opts, cheb_game_result *res, void *stream)
 {
+    NvtxRange nvtx_range("game_solve");
     tl_ctx = ctx;
     if (!ctx) return fail(CHEB_EINVAL, "null context");
     if (batch < 1 || !params || !opts || !res) return fail(CHEB_EINVAL, "game_solve: bad batch or null arrays");
@@ -707,6 +710,9 @@ extern "C" CHEB_API cheb_status game_solve(cheb_ctx *ctx, int32_t batch, const c
     for (auto &g : groups) {
         int NP = 1;
         for (int t = 0; t < g.J; ++t) NP *= g.n;
+        const std::string label = "game_solve group J=" + std::to_string(g.J) + " n=" + std::to_string(g.n) +
+                                  " prec=" + std::to_string(g.prec) + " batch=" + std::to_string(g.members.size());
+        NvtxRange group_range(label.c_str());
         cheb_status r = solve_group(ctx, g.J, g.n, NP, g.prec, g.general, g.n_u, g.members, params, opts, res, st);
         if (r) return r;
     }

@@ -171,6 +171,8 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     const int nl = threadIdx.x / kDfGroup, grp = threadIdx.x % kDfGroup;
     const int j = blockIdx.x * kDfNodes + nl;
     const int J = g.J, n = g.n, NP = g.NP;
+    // the node's rows fit the static arrays (uniform)
+    if (!CHEB_DCHECK(n <= kGameNMax && J >= 2 && J <= 4)) return;
     const bool valid = j < NP;
     const int jc = valid ? j : NP - 1;
     // mode strides of C_i (row-major) and the modes other than i, by arithmetic
@@ -371,6 +373,8 @@ refit_df_kernel(const void *__restrict__ Xv, const double *__restrict__ M, void 
     const int64_t total = G * R;
     const int64_t r0 = (int64_t)blockIdx.x * kRfRows;
     const int rows = (int)((total - r0) < kRfRows ? (total - r0) : kRfRows);
+    // the staged rows and columns fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK(sizeof(dfl) * (size_t)(kRfRows * ns + 4 * Q * n) <= dyn_smem_bytes() && r0 < total)) return;
     if (stats) {
         bool any = false;
         for (int64_t g = r0 / R; g <= (r0 + rows - 1) / R; ++g) any = any || !stats[g / J].done;

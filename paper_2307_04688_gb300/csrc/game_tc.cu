@@ -259,11 +259,14 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
 #pragma unroll
             for (int k = 0; k < S::E; ++k) {
                 const int ka = kc * S::E + k;
-                v[k] = (ok && ka < S::NM) ? (float)C[ki * si + ka * sa + roff] : 0.0f;
+                v[k] = (ok && ka < S::NM && CHEB_DCHECK(ki * si + ka * sa + roff < S::NPOW))
+                           ? (float)C[ki * si + ka * sa + roff]
+                           : 0.0f;
             }
         }
-        uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES + (size_t)c * S::CHUNK_BYTES +
-                       (size_t)kc * (S::NC * 16) + (size_t)row * 16;
+        const size_t off = (size_t)c * S::CHUNK_BYTES + (size_t)kc * (S::NC * 16) + (size_t)row * 16;
+        if (!CHEB_DCHECK(off + (size_t)(F::SB - 1) * S::SPLIT_BYTES + 16 <= (size_t)S::NCH * S::CHUNK_BYTES)) continue;
+        uint8_t *dst = static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES + off;
         split_store16<FORM, F::SB>(v, dst, S::SPLIT_BYTES);
     }
     if constexpr (S::TAIL) {
@@ -281,7 +284,9 @@ __global__ void game_bprep_kernel(const GameDev *__restrict__ insts, const GameS
             const int si = mode_stride<JJ, NN>(i), sa = mode_stride<JJ, NN>(o[0]), sb = mode_stride<JJ, NN>(o[1]);
             const double *C = g.C + (size_t)i * g.NP;
             const int ki = e / S::CAP, k = e - ki * S::CAP;
-            const float v = k < NN ? (float)C[ki * si + (NN - 1) * sa + k * sb] : 0.0f;   // Ca[ki][kb = k]
+            const float v = (k < NN && CHEB_DCHECK(ki * si + (NN - 1) * sa + k * sb < S::NPOW))
+                                ? (float)C[ki * si + (NN - 1) * sa + k * sb]
+                                : 0.0f;   // Ca[ki][kb = k]
             float *dst = reinterpret_cast<float *>(static_cast<uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES +
                                                    (size_t)S::NCH * S::CHUNK_BYTES);
             dst[e] = v;
@@ -331,6 +336,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the carve-up above fits the dynamic shared memory (uniform: all or none return)
+    if (!CHEB_DCHECK((uint32_t)(reinterpret_cast<uint8_t *>(abort_flag + 1) - smem) <= dyn_smem_bytes())) return;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -497,6 +504,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     while (item < items) {
         int t, i, q;
         decode(item, t, i, q);
+        if (!CHEB_DCHECK(q < B && i < JJ && t < tiles)) break;   // uniform across the block
         GameStat *st = &stats[q];
         const GameDev &g = insts[q];
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
@@ -556,7 +564,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int col = g16 * 16 + e;
-                        if (col < kis) w_s[(c * S::CHKI + col) * kTile + r] = __uint_as_float(v[e]);
+                        if (col < kis && CHEB_DCHECK(c * S::CHKI + col < NN))
+                            w_s[(c * S::CHKI + col) * kTile + r] = __uint_as_float(v[e]);
                     }
                 }
             } else if constexpr (JJ == 4) {
@@ -576,7 +585,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                             if (rr < NN * NN) acc = fmaf(__uint_as_float(v[e]), Tb4[rr / N4] * Tc4[rr % N4], acc);
                         }
                     }
-                    w_s[(c * S::CHKI + kl) * kTile + r] = acc;
+                    if (CHEB_DCHECK(c * S::CHKI + kl < NN)) w_s[(c * S::CHKI + kl) * kTile + r] = acc;
                 }
             } else {
                 const int r = quarter * 32 + lane;
@@ -609,7 +618,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                         }
                         acc = fmaf(ta_last, ta_dot, fmaf(tb_last, __uint_as_float(vt), acc));
                     }
-                    w_s[(c * S::CHKI + kl) * kTile + r] = acc;
+                    if (CHEB_DCHECK(c * S::CHKI + kl < NN)) w_s[(c * S::CHKI + kl) * kTile + r] = acc;
                 }
             }
             tc_fence_before();

@@ -332,6 +332,11 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const GemmP p)
     const int nt = blockIdx.x, mt = blockIdx.y, z = blockIdx.z;
     const int kt0 = z * p.kt_per;
     const int nk = min(p.kt_per, p.kt_total - kt0);
+    // the operand stages fit the dynamic shared memory, the tile lies in the
+    // output, the K tiles in both packed operands (uniform: all or none return)
+    if (!CHEB_DCHECK(kGemmSmem <= (int)dyn_smem_bytes() && mt * kTM < p.o.M && nt * kTN < p.o.N &&
+                     kt0 + nk <= p.a_kt && kt0 + nk <= p.b_kt))
+        return;
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -1033,6 +1038,7 @@ extern "C" {
 CHEB_API cheb_status surrogate_create(cheb_ctx *ctx, int32_t n_in, int32_t width, int32_t depth, int32_t n_out,
                                       uint64_t seed, cheb_mlp **out)
 {
+    NvtxRange nvtx_range("surrogate_create");
     if (!ctx || !out) return fail(CHEB_EINVAL, "null argument");
     if (n_in < 1 || width < 1 || depth < 0 || n_out < 1 || depth > 16 || width > 8192 || n_out > 1 << 20 ||
         n_in > 8192)
@@ -1131,6 +1137,7 @@ CHEB_API cheb_status surrogate_create(cheb_ctx *ctx, int32_t n_in, int32_t width
 
 CHEB_API cheb_status surrogate_destroy(cheb_mlp *net)
 {
+    NvtxRange nvtx_range("surrogate_destroy");
     if (!net) return CHEB_OK;
     cudaSetDevice(net->device);
     cudaDeviceSynchronize();
@@ -1170,6 +1177,7 @@ CHEB_API cheb_status surrogate_params(cheb_mlp *net, float *get, const float *se
 CHEB_API cheb_status surrogate_loss_grad(cheb_ctx *ctx, cheb_mlp *net, const float *X, const float *T, int32_t B,
                                          float *loss, float *grad, void *stream)
 {
+    NvtxRange nvtx_range("surrogate_loss_grad");
     cheb_status r = check_net(ctx, net);
     if (r) return r;
     if (B < 1 || !X || !T) return fail(CHEB_EINVAL, "surrogate_loss_grad: bad batch");
@@ -1191,6 +1199,7 @@ CHEB_API cheb_status surrogate_loss_grad(cheb_ctx *ctx, cheb_mlp *net, const flo
 
 CHEB_API cheb_status surrogate_adam_step(cheb_ctx *ctx, cheb_mlp *net, const float *grad, float lr, void *stream)
 {
+    NvtxRange nvtx_range("surrogate_adam_step");
     cheb_status r = check_net(ctx, net);
     if (r) return r;
     if (!(lr > 0)) return fail(CHEB_EINVAL, "surrogate_adam_step: lr must be > 0");
@@ -1214,6 +1223,7 @@ CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double 
                                      const double *Y, int64_t y_stride, int64_t S, int32_t epochs, int32_t batch,
                                      float lr, uint64_t seed, float *loss_per_epoch, void *stream)
 {
+    NvtxRange nvtx_range("surrogate_train");
     cheb_status r = check_net(ctx, net);
     if (r) return r;
     const int F = net->dims[0], O = net->dims[net->L];
@@ -1350,6 +1360,7 @@ CHEB_API cheb_status surrogate_train(cheb_ctx *ctx, cheb_mlp *net, const double 
 CHEB_API cheb_status surrogate_predict(cheb_ctx *ctx, cheb_mlp *net, const double *X, int64_t x_stride, int64_t P,
                                        double *Y, int64_t y_stride, void *stream)
 {
+    NvtxRange nvtx_range("surrogate_predict");
     cheb_status r = check_net(ctx, net);
     if (r) return r;
     const int F = net->dims[0], O = net->dims[net->L];

@@ -79,6 +79,7 @@ extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc(int d, const int32_t *n, 
                                                        const int32_t *m, const double *const *x,
                                                        float *out, cheb_precision prec, void *stream)
 {
+    NvtxRange nvtx_range("cheb_eval_grid_noalloc");
     tl_ctx = nullptr;
     if (prec != CHEB_TF32X3 && prec != CHEB_BF16X3 && prec != CHEB_BF16X6)
         return fail(CHEB_EINVAL, "cheb_eval_grid_noalloc: prec must be a split form");
@@ -184,5 +185,9 @@ extern "C" CHEB_API cheb_status cheb_eval_grid_noalloc_status(void *stream)
     CHEB_CUDA_TRY(cudaStreamSynchronize(sm));
     CHEB_CUDA_TRY(cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost));
     if (v != 0) return fail((cheb_status)v, "cheb_eval_grid_noalloc: a device-side wait ran out of time");
+#ifdef CHEB_CHECK
+    return dcheck::report();
+#else
     return CHEB_OK;
+#endif
 }

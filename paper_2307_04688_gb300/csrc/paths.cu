@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(kThreads) game_paths_kernel(const PathParams P
     __shared__ double ps[4], us[4];
     const int tid = threadIdx.x, J = P.J, n = P.n;
     const int64_t NP = P.len1 * n, T = P.T;
+    // the rows and both contraction buffers fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK(sizeof(double) * (4 * (size_t)kMaxN + (size_t)P.len1 + (size_t)(P.len1 / n > 0 ? P.len1 / n : 1)) <=
+                         dyn_smem_bytes() && n <= kMaxN && J <= 4))
+        return;
     for (int64_t k = blockIdx.x; k < P.K; k += gridDim.x) {
         if (tid < J) {
             ps[tid] = P.p0[k * J + tid];
@@ -134,6 +138,7 @@ extern "C" CHEB_API cheb_status game_paths(cheb_ctx *ctx, const cheb_game_params
                                            const double *p0, int64_t T, double *p_path, double *u_path,
                                            void *stream)
 {
+    NvtxRange nvtx_range("game_paths");
     if (!ctx) return fail(CHEB_EINVAL, "null context");
     tl_ctx = ctx;
     if (!params || !opts) return fail(CHEB_EINVAL, "game_paths: null params or opts");

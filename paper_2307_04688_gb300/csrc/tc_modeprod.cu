@@ -159,6 +159,8 @@ modeprod_tc_kernel(const Params P)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntiles = (P.R + kTileM - 1) / kTileM;
+    // the carve-up above fits the dynamic shared memory (uniform: all or none return)
+    if (!CHEB_DCHECK((uint32_t)(reinterpret_cast<uint8_t *>(abort_flag + 1) - smem) <= dyn_smem_bytes())) return;
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -190,11 +192,13 @@ modeprod_tc_kernel(const Params P)
                 const int k = c * E + e;
                 v[e] = (j < m && k < n) ? (float)P.B[(int64_t)j * n + k] : 0.0f;
             }
-            split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+            if (CHEB_DCHECK((uint32_t)(c * Np + j) * 16 + 16 <= b_split_bytes))
+                split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
         }
         for (int t = tid; t < P.tail * Np; t += kThreads) {
             const int q = t / Np, j = t - q * Np;
-            sBt[q * Np + j] = j < m ? (float)P.B[(int64_t)j * n + Kp + q] : 0.0f;
+            if (CHEB_DCHECK(q * Np + j < kMaxTail * kMaxM && Kp + q < n))
+                sBt[q * Np + j] = j < m ? (float)P.B[(int64_t)j * n + Kp + q] : 0.0f;
         }
     } else {
         for (int j = tid; j < Np; j += kThreads) {
@@ -220,7 +224,8 @@ modeprod_tc_kernel(const Params P)
                     }
                     v[e] = (j < m && k < n) ? tk : 0.0f;
                 }
-                split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
+                if (CHEB_DCHECK((uint32_t)(c * Np + j) * 16 + 16 <= b_split_bytes))
+                    split_store_chunk<FORM, SB>(v, sB + (uint32_t)c * Np * 16 + j * 16, b_split_bytes);
             }
             // the tail columns continue the same recurrence
             for (int q = 0; q < P.tail; ++q) {
@@ -234,7 +239,7 @@ modeprod_tc_kernel(const Params P)
                     t1 = t2;
                     tk = t2.hi + t2.lo;
                 }
-                sBt[q * Np + j] = j < m ? tk : 0.0f;
+                if (CHEB_DCHECK(q * Np + j < kMaxTail * kMaxM)) sBt[q * Np + j] = j < m ? tk : 0.0f;
             }
         }
     }
@@ -252,6 +257,8 @@ modeprod_tc_kernel(const Params P)
     auto tile_full = [&](int64_t t) { return (t + 1) * kTileM <= P.R; };
     auto issue_load = [&](int64_t t, int buf) {
         const uint32_t bytes = (uint32_t)(kTileM * n * sizeof(XT));
+        // a skipped copy leaves its barrier incomplete: the bounded wait gives up
+        if (!CHEB_DCHECK((t + 1) * kTileM <= P.R && buf < kStages && bytes <= stage_bytes)) return;
         mbar_arrive_expect_tx(&bars[buf], bytes);
         bulk_g2s(sX + buf * stage_bytes, X + t * kTileM * (int64_t)n, bytes, &bars[buf]);
     };
@@ -297,7 +304,7 @@ modeprod_tc_kernel(const Params P)
         // thread runs for the same row
         float xt[kMaxTail];
         {
-            const bool valid = row < rows;
+            const bool valid = row < rows && CHEB_DCHECK(tile * kTileM + row < P.R);
             const XT *xr = xs + row * n;
 #pragma unroll
             for (int q = 0; q < kMaxTail; ++q) xt[q] = (valid && q < P.tail) ? to_f32(xr[Kp + q]) : 0.0f;
@@ -316,6 +323,7 @@ modeprod_tc_kernel(const Params P)
                     const int k = (c0 + 2) * E + e;
                     v1[e] = (valid && two && k < n) ? to_f32(xr[k]) : 0.0f;
                 }
+                if (!CHEB_DCHECK((uint32_t)((two ? c0 + 2 : c0) * kTileM + row) * 16 + 16 <= a_split_bytes)) break;
                 split_store_chunk<FORM, SA>(v0, sA + (uint32_t)c0 * (kTileM * 16) + row * 16, a_split_bytes);
                 if (two)
                     split_store_chunk<FORM, SA>(v1, sA + (uint32_t)(c0 + 2) * (kTileM * 16) + row * 16, a_split_bytes);
@@ -359,7 +367,7 @@ modeprod_tc_kernel(const Params P)
         // epilogue: rows 32*quarter + lane, column chunks ehalf, ehalf + 2, ...
         {
             const int r = quarter * 32 + lane;
-            const bool valid = r < rows;
+            const bool valid = r < rows && CHEB_DCHECK(tile * kTileM + r < P.R);
             const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
             float *o = P.out + tile * kTileM + r;
             for (int c0 = ehalf * 16; c0 < Np; c0 += 32) {
@@ -395,7 +403,7 @@ modeprod_tc_kernel(const Params P)
                     const int lim = m - c0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        if (q < lim) *oc = y[q];
+                        if (q < lim && CHEB_DCHECK(c0 + q < m)) *oc = y[q];
                         oc += P.R;
                     }
                 }
