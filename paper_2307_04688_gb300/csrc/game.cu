@@ -517,8 +517,11 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
         CHEB_CUDA_TRY(cudaGetLastError());
         if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, df_refit, s))) return e;
         {
-            ProfScope prof("game_commit", s);
+            ProfScope prof("game_commit_copy", s);
             commit_copy_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);
+        }
+        {
+            ProfScope prof("game_commit_stat", s);
             commit_stat_kernel<<<(B + 127) / 128, 128, 0, s>>>(d_inst, d_stat, B);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
@@ -532,11 +535,12 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
         if ((r = game_tc_tune(ctx, d_inst, d_stat, B, J, n, prec, st))) return r;
     }
 
-    // ---- chunks of iterations, captured once into a CUDA graph ----
+    // ---- chunks of iterations, captured once into a CUDA graph; with kernel
+    // timing on, the timing events become event-record nodes of the graph, so
+    // the kernels are timed where the graph runs them (the last chunk's launches)
     const int chunk = (int)std::min<int64_t>(max_iter, 32);
-    const bool use_graph = !ctx->prof_on;
     cudaGraphExec_t exec = nullptr;
-    if (use_graph) {
+    {
         cudaStream_t cs = nullptr;
         CHEB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
@@ -563,14 +567,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
     cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
     auto launch_chunk = [&](int slot) -> cheb_status {
-        if (use_graph) {
-            CHEB_CUDA_TRY(cudaGraphLaunch(exec, st));
-        } else {
-            for (int t = 0; t < chunk; ++t) {
-                cheb_status e = enqueue_iteration(st);
-                if (e) return e;
-            }
-        }
+        CHEB_CUDA_TRY(cudaGraphLaunch(exec, st));
         CHEB_CUDA_TRY(cudaMemcpyAsync(hs + slot * B, d_stat, sizeof(GameStat) * B, cudaMemcpyDeviceToHost, st));
         CHEB_CUDA_TRY(cudaEventRecord(ev[slot], st));
         return CHEB_OK;

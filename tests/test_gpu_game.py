@@ -429,3 +429,25 @@ def test_split_two_players_full_solve_with_polish(ctx):
                             raise_on_error=False)
     assert r[0].status == 0 and r[0].residual < 1e-10 and r[0].iters_split > 0
     assert rel(V[0].cpu().numpy(), Vf[0].cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("prec,polish", [("bf16x6", 1), ("bf16x6", 2), ("df64", 0), ("fp64", 0)])
+def test_solves_are_bit_reproducible(ctx, prec, polish):
+    """Every reduction of the iteration has a fixed order (the residual is an integer max of
+    FP64 bit patterns), so a solve is deterministic: two solves of the same mixed batch (two
+    size classes, instances that stop at different iterations, the split phase, the switch to
+    the polish and the polish phase) give bit-identical coefficients, controls, iteration
+    counts and residuals."""
+    rng = I.SplitMix64(123)
+    ps = [I.draw_game_params(rng, 3) for _ in range(5)]
+    ns = [9, 17, 9, 17, 9]
+    its = [400, 100000, 37, 250, 100000]
+    opts = [cb.game_opts(k, tol=1e-10, max_iter=m, prec=prec, polish_fp64=polish) for k, m in zip(ns, its)]
+    V1, u1, r1 = cb.game_solve(ctx, ps, opts, raise_on_error=False)
+    V2, u2, r2 = cb.game_solve(ctx, ps, opts, raise_on_error=False)
+    for q in range(5):
+        assert torch.equal(V1[q], V2[q]) and torch.equal(u1[q], u2[q]), q
+        assert (r1[q].iters, r1[q].iters_split, r1[q].status) == (r2[q].iters, r2[q].iters_split, r2[q].status)
+        assert r1[q].residual == r2[q].residual
+        assert r1[q].iters <= its[q]
+    ctx.device_status()
