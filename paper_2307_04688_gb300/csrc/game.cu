@@ -73,7 +73,7 @@ __global__ void next_state_kernel(const GameDev *__restrict__ insts, const GameS
                 if (t < J && t != l) coup += g.K[l * J + t] * (pb[t] - pb[l]);
             const double dyn = coup * g.minv - g.c[l] * pb[l] + g.beta[l] * g.u[l * NP + j];
             const double q = pb[l] + g.h * dyn;
-            g.X[l * NP + j] = 2.0 * q / P_M - 1.0;
+            g.X[l * NP + j] = g.two_over_PM * q - 1.0;
         }
     }
 }
@@ -220,7 +220,7 @@ __global__ void restart_kernel(const GameDev *__restrict__ insts, const GameStat
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         g.u[t] = 0.0;
         g.Vn[t] = 0.0;
-        g.Vn_new[t] = 0.0;
+        store_vn_new(g, t, 0.0);
         g.C[t] = 0.0;
     }
 }
@@ -279,8 +279,9 @@ __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0,
     const GameDev g = insts[blockIdx.y];
     const int total = g.J * g.NP;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        g.Vn_new[t] = (has_v0 && g.V0) ? g.V0[t] : 0.0;
-        g.Vn[t] = g.Vn_new[t];
+        const double v = (has_v0 && g.V0) ? g.V0[t] : 0.0;
+        store_vn_new(g, t, v);
+        g.Vn[t] = v;
         g.u[t] = (has_u0 && g.u0) ? fmin(fmax(g.u0[t], 0.0), g.U_M) : 0.0;
     }
 }
@@ -296,23 +297,27 @@ __global__ void init_state_kernel(const GameDev *__restrict__ insts, int has_v0,
 // its original mode order, the last one written straight into C. With
 // `stats`, slabs of finished instances are skipped: their coefficients stay as
 // last fitted, which is what a refit of their unchanged Vn_new would give.
-// Large split-precision groups (`df`) refit in double-float on the FP32 pipe
-// instead (game_refit_df, relative error about 2^-47): on GB300 the FP64
-// refit was a quarter of a batched n = 33 iteration.
+// Split-precision groups (`Vdf`, the (hi, lo) pairs of Vn_new) refit in
+// double-float on the FP32 pipe instead (relative error about 2^-47; the FP64
+// pipe runs at ~1.25 TFLOP/s): small groups in one launch (game_refit_df_chain),
+// larger ones one launch per mode (game_refit_df).
 static_assert(offsetof(GameStat, done) == 0 && sizeof(GameStat) % sizeof(int) == 0, "GameStat layout");
 static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const double *Vn_new_all,
-                               double *C_all, double *tmp0, double *tmp1, const GameStat *stats, bool df,
-                               cudaStream_t st)
+                               const float *Vdf_all, double *C_all, double *tmp0, double *tmp1,
+                               const GameStat *stats, cudaStream_t st)
 {
     const double *M = nullptr;
     cheb_status r = dct_matrix(ctx, n, &M);
     if (r) return r;
-    // double-float only where its 64-row tiles fill the GPU twice over: below
-    // that the FP64 product (one thread per output for small problems) has
-    // the shorter latency
-    const int64_t tiles = ((int64_t)G * (NP / n) + 63) / 64;
-    if (df && game_refit_df_supported(n) && tiles >= 2 * (int64_t)ctx->num_sms)
-        return game_refit_df(Vn_new_all, M, C_all, tmp0, tmp1, G, J, n, NP, stats, st);
+    const bool small = G * n <= 8 * ctx->num_sms;
+    if (Vdf_all) {
+        if (small) {
+            r = game_refit_df_chain(Vdf_all, M, C_all, G, J, n, stats, st);
+            if (r != CHEB_EUNSUPPORTED) return r;
+        }
+        if (game_refit_df_supported(n))
+            return game_refit_df(Vdf_all, M, C_all, tmp0, tmp1, G, J, n, NP, stats, st);
+    }
     SlabSkip sk;
     if (stats) {
         sk.flags = &stats->done;
@@ -320,7 +325,7 @@ static cheb_status refit_group(cheb_ctx *ctx, int G, int J, int n, int NP, const
         sk.per_flag = J;
     }
     // small groups: all J products in one launch with the intermediates in shared memory
-    if (G * n <= 8 * ctx->num_sms) {
+    if (small) {
         r = modeprod_f64_chain(Vn_new_all, M, C_all, G, J, n, sk, st);
         if (r != CHEB_EUNSUPPORTED) return r;
     }
@@ -347,8 +352,10 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
     size_t bytes = 0;
     auto rnd = [](size_t x) { return (x + 255) & ~size_t(255); };
     const bool any_df = prec == CHEB_DF64 || (prec != CHEB_FP64 && opts[members[0]].polish_fp64 == 1);
-    bytes += 9 * rnd(arr) + (any_df ? rnd(arr) : 0) + rnd(sizeof(double) * 128) + rnd(sizeof(GameDev) * B) +
-             rnd(sizeof(GameStat) * B) + rnd(tc_bytes);
+    // split-precision groups refit in double-float from (hi, lo) pairs of Vn_new
+    const bool df_refit = prec != CHEB_FP64 && prec != CHEB_DF64;
+    bytes += 9 * rnd(arr) + (any_df ? rnd(arr) : 0) + (df_refit ? rnd(arr) : 0) + rnd(sizeof(double) * 128) +
+             rnd(sizeof(GameDev) * B) + rnd(sizeof(GameStat) * B) + rnd(tc_bytes);
     cheb_status r = ctx->game.reserve(bytes);
     if (r) return r;
     uint8_t *base = static_cast<uint8_t *>(ctx->game.ptr);
@@ -372,6 +379,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
     GameStat *d_stat = reinterpret_cast<GameStat *>(take(sizeof(GameStat) * B));
     uint8_t *tc_ws = take(tc_bytes);
     float *Cdf_all = any_df ? reinterpret_cast<float *>(take(arr)) : nullptr;   // (hi, lo) per coefficient
+    float *Vdf_all = df_refit ? reinterpret_cast<float *>(take(arr)) : nullptr;  // (hi, lo) per nodal value
     (void)init;
 
     // nodes cos(pi k / N) (the integer argument is exact); for the general
@@ -423,6 +431,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
         g.h = o.h;
         g.delta = 1.0 - p.rho * o.h;
         g.P_M = o.P_M;
+        g.two_over_PM = 2.0 / o.P_M;
         for (int t = 0; t < J; ++t) {
             g.slope[t] = 2.0 * o.h * p.beta[t] / o.P_M;
             g.hA[t] = o.h * p.A[t];
@@ -434,6 +443,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
         g.polish = o.polish_fp64 != 0;
         g.polish_mode = o.polish_fp64 == 2 ? 0 : 2;
         g.Cdf = Cdf_all ? Cdf_all + 2 * per * q : nullptr;
+        g.Vdf = Vdf_all ? Vdf_all + 2 * per * q : nullptr;
         g.stall_window = 200;
         g.C = C_all + per * q;
         g.u = u_all + per * q;
@@ -470,12 +480,14 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
     const unsigned copy_blocks = (unsigned)std::min<int64_t>(((int64_t)per + 255) / 256, 256);
     init_state_kernel<<<dim3(copy_blocks, B), 256, 0, st>>>(d_inst, any_v0, any_u0);
     CHEB_CUDA_TRY(cudaGetLastError());
-    const bool df_refit = prec != CHEB_FP64 && prec != CHEB_DF64;
-    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, nullptr, df_refit, st))) return r;
+    if ((r = refit_group(ctx, B * J, J, n, NP, Vn_new_all, Vdf_all, C_all, fit0, fit1, nullptr, st))) return r;
     if (general && (r = game_general_prepare(ctx, d_inst, B, J, NP, n_u, Gc_all, gtmp0, gtmp1, st))) return r;
 
     // ---- one iteration ----
-    const unsigned node_blocks = (unsigned)((NP + 127) / 128);
+    // next states: 32-thread blocks for small groups, so that their FP64 work
+    // spreads over the SMs
+    const int ns_threads = (int64_t)NP * B <= 32768 ? 32 : 128;
+    const unsigned node_blocks = (unsigned)((NP + ns_threads - 1) / ns_threads);
     // the FP64 player update: 32 nodes per block, their J - 1 Chebyshev rows and
     // w in shared memory
     const unsigned f64_blocks = (unsigned)((NP + kF64Nodes - 1) / kF64Nodes);
@@ -500,7 +512,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
             if ((e = game_general_player(d_inst, d_stat, B, J, NP, s))) return e;
         } else {
             ProfScope prof("game_next_state", s);
-            next_state_kernel<<<dim3(node_blocks, B), 128, 0, s>>>(d_inst, d_stat);
+            next_state_kernel<<<dim3(node_blocks, B), ns_threads, 0, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
         const bool split = prec != CHEB_FP64 && prec != CHEB_DF64;
@@ -515,7 +527,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
             player_f64_kernel<<<dim3(f64_blocks, J, B), 128, f64_smem, s>>>(d_inst, d_stat);
         }
         CHEB_CUDA_TRY(cudaGetLastError());
-        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, C_all, fit0, fit1, d_stat, df_refit, s))) return e;
+        if ((e = refit_group(ctx, B * J, J, n, NP, Vn_new_all, Vdf_all, C_all, fit0, fit1, d_stat, s))) return e;
         {
             ProfScope prof("game_commit_copy", s);
             commit_copy_kernel<<<dim3(copy_blocks, B), 256, 0, s>>>(d_inst, d_stat);
@@ -530,7 +542,7 @@ cheb_status solve_group(cheb_ctx *ctx, int J, int n, int NP, int prec, int gener
 
     // ---- tile shapes of the split player update, timed on this group ----
     if (prec != CHEB_FP64 && prec != CHEB_DF64) {
-        next_state_kernel<<<dim3(node_blocks, B), 128, 0, st>>>(d_inst, d_stat);
+        next_state_kernel<<<dim3(node_blocks, B), ns_threads, 0, st>>>(d_inst, d_stat);
         CHEB_CUDA_TRY(cudaGetLastError());
         if ((r = game_tc_tune(ctx, d_inst, d_stat, B, J, n, prec, st))) return r;
     }

@@ -342,7 +342,7 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     us = bu;
     us = fmin(fmax(us, 0.0), g.U_M);
     g.u_new[i * NP + j] = us;
-    g.Vn_new[i * NP + j] = V;
+    store_vn_new(g, i * NP + j, V);
     const double d = fabs(V - g.Vn[i * NP + j]);
     atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
 }
@@ -352,18 +352,18 @@ game_player_df_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 // on the FP32 pipe, the same slab-wise product as the FP64 refit:
 // out[(g n + j) R + r] = sum_k M[j, k] X[g R + r, k] over G slabs (slab g =
 // player g % J of instance g / J) of R rows, slabs of finished instances
-// skipped (stats null: none). Between the J modes the values stay
-// double-float pairs (8 bytes, like the FP64 values they replace): the first
-// mode reads FP64 values (IN_D), the last writes FP64 coefficients (OUT_D).
-// A block takes 64 rows and all 4Q >= n output columns; each thread one row
-// and Q columns, every product error-free and every sum compensated, so a
-// coefficient carries a relative error of about 2^-47 (the split forms' own
-// is above 2^-24).
+// skipped (stats null: none). The input is double-float pairs: the players'
+// (hi, lo) split of Vn_new for the first mode, then the previous mode's
+// output (8 bytes per value, like the FP64 values they replace); the last
+// mode writes FP64 coefficients (OUT_D). A block takes 64 rows and all
+// 4Q >= n output columns; each thread one row and Q columns, every product
+// error-free and every sum compensated, so a coefficient carries a relative
+// error of about 2^-47 (the split forms' own is above 2^-24).
 constexpr int kRfRows = 64, kRfThreads = 256;
 
-template <int Q, bool IN_D, bool OUT_D>
+template <int Q, bool OUT_D>
 __global__ void __launch_bounds__(kRfThreads, 4)
-refit_df_kernel(const void *__restrict__ Xv, const double *__restrict__ M, void *__restrict__ outv, int64_t G,
+refit_df_kernel(const dfl *__restrict__ X, const double *__restrict__ M, void *__restrict__ outv, int64_t G,
                 int64_t R, int n, const GameStat *__restrict__ stats, int J)
 {
     extern __shared__ dfl rsm[];
@@ -382,8 +382,7 @@ refit_df_kernel(const void *__restrict__ Xv, const double *__restrict__ M, void 
     }
     for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
         const int rr = t / n, k = t - rr * n;
-        sX[rr * ns + k] = IN_D ? df_of(static_cast<const double *>(Xv)[r0 * n + t])
-                               : static_cast<const dfl *>(Xv)[r0 * n + t];
+        sX[rr * ns + k] = X[r0 * n + t];
     }
     for (int t = threadIdx.x; t < (kRfRows - rows) * n; t += blockDim.x) {
         const int rr = rows + t / n, k = t % n;
@@ -421,34 +420,87 @@ refit_df_kernel(const void *__restrict__ Xv, const double *__restrict__ M, void 
 }
 
 template <int Q>
-cheb_status refit_df_mode(const void *X, bool in_d, const double *M, void *out, bool out_d, int64_t G, int64_t R,
-                          int n, const GameStat *stats, int J, cudaStream_t st)
+cheb_status refit_df_mode(const dfl *X, const double *M, void *out, bool out_d, int64_t G, int64_t R, int n,
+                          const GameStat *stats, int J, cudaStream_t st)
 {
     const int64_t tiles = (G * R + kRfRows - 1) / kRfRows;
     if (tiles > 0x7fffffffLL) return fail(CHEB_EUNSUPPORTED, "refit: too many rows");
     const size_t smem = sizeof(dfl) * (size_t)(kRfRows * (n | 1) + 4 * Q * n);
     const unsigned grid = (unsigned)tiles;
-    if (in_d && out_d)
-        refit_df_kernel<Q, true, true><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
-    else if (in_d)
-        refit_df_kernel<Q, true, false><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
-    else if (out_d)
-        refit_df_kernel<Q, false, true><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+    if (out_d)
+        refit_df_kernel<Q, true><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
     else
-        refit_df_kernel<Q, false, false><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
+        refit_df_kernel<Q, false><<<grid, kRfThreads, smem, st>>>(X, M, out, G, R, n, stats, J);
     CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
+}
+
+// All J modes of the double-float refit of a slab in one CTA per (slab g,
+// last output index k_J), for small groups (a single game refits 3 slabs:
+// the J launches above would leave most SMs idle and each pay a launch).
+// The first product (the last mode) is taken for this k_J only and the other
+// J - 1 run on the resulting n^(J-1) pairs in shared memory, each moving its
+// new index to the front as refit_df_kernel does. Every output is the same
+// compensated dot product over k in the same order, and every intermediate
+// the same renormalised pair, as in the J launches of refit_df_kernel, so the
+// coefficients are bit-identical to game_refit_df's.
+constexpr int kRfChainMax = 4913;   // largest n^(J-1) held in shared memory
+constexpr int kRfChainThreads = 256;
+
+__global__ void __launch_bounds__(kRfChainThreads)
+refit_df_chain_kernel(const dfl *__restrict__ V, const double *__restrict__ M, double *__restrict__ C, int J, int n,
+                      const GameStat *__restrict__ stats)
+{
+    extern __shared__ dfl chain_df[];
+    const int kJ = blockIdx.x;
+    const int64_t g = blockIdx.y;
+    if (stats && stats[g / J].done) return;
+    int R = 1;
+    for (int s = 0; s < J - 1; ++s) R *= n;
+    dfl *sM = chain_df;
+    dfl *cur = sM + n * n, *nxt = cur + R;
+    // M and the two intermediates fit the dynamic shared memory (uniform)
+    if (!CHEB_DCHECK(sizeof(dfl) * (size_t)(n * n + 2 * R) <= dyn_smem_bytes() && kJ < n)) return;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sM[t] = df_of(M[t]);
+    __syncthreads();
+    // the last mode: cur[r] = sum_k M[k_J, k] V_g[r, k]
+    const dfl *Vg = V + g * (int64_t)R * n;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const dfl *xr = Vg + (int64_t)r * n;
+        dacc acc;
+        for (int k = 0; k < n; ++k) df_mac(acc, sM[kJ * n + k], xr[k]);
+        cur[r] = df_done(acc);
+    }
+    __syncthreads();
+    // the other modes: cur as [R / n rows x n], nxt[j (R / n) + r] = sum_k M[j, k] cur[r n + k]
+    const int Rp = R / n;
+    for (int step = 1; step < J; ++step) {
+        for (int t = threadIdx.x; t < n * Rp; t += blockDim.x) {
+            const int j = t / Rp, r = t - j * Rp;
+            const dfl *xr = cur + r * n;
+            dacc acc;
+            for (int k = 0; k < n; ++k) df_mac(acc, sM[j * n + k], xr[k]);
+            nxt[t] = df_done(acc);
+        }
+        __syncthreads();
+        dfl *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    // cur = C_g[k_1 .. k_{J-1}, k_J] for this k_J, (k_1 .. k_{J-1}) row-major
+    double *og = C + g * (int64_t)R * n;
+    for (int t = threadIdx.x; t < R; t += blockDim.x) og[(int64_t)t * n + kJ] = df_val(cur[t]);
 }
 
 }  // namespace
 
 bool game_refit_df_supported(int n) { return n == 5 || n == 9 || n == 17 || n == 33; }
 
-cheb_status game_refit_df(const double *V, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
+cheb_status game_refit_df(const float *Vdf, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
                           int n, int NP, const GameStat *stats, cudaStream_t st)
 {
     if (!game_refit_df_supported(n)) return fail(CHEB_EUNSUPPORTED, "double-float refit: n not in {5, 9, 17, 33}");
-    const void *src = V;
+    const dfl *src = reinterpret_cast<const dfl *>(Vdf);
     double *bufs[2] = {tmp0, tmp1};
     ProfScope prof("game_refit_df n=" + std::to_string(n), st);
     for (int t = 0; t < J; ++t) {
@@ -457,14 +509,37 @@ cheb_status game_refit_df(const double *V, const double *M, double *C, double *t
         const int64_t R = NP / n;
         cheb_status r;
         switch (n) {
-        case 5: r = refit_df_mode<2>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
-        case 9: r = refit_df_mode<3>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
-        case 17: r = refit_df_mode<5>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
-        default: r = refit_df_mode<9>(src, t == 0, M, dst, last, G, R, n, stats, J, st); break;
+        case 5: r = refit_df_mode<2>(src, M, dst, last, G, R, n, stats, J, st); break;
+        case 9: r = refit_df_mode<3>(src, M, dst, last, G, R, n, stats, J, st); break;
+        case 17: r = refit_df_mode<5>(src, M, dst, last, G, R, n, stats, J, st); break;
+        default: r = refit_df_mode<9>(src, M, dst, last, G, R, n, stats, J, st); break;
         }
         if (r) return r;
-        src = dst;
+        src = static_cast<const dfl *>(dst);
     }
+    return CHEB_OK;
+}
+
+cheb_status game_refit_df_chain(const float *Vdf, const double *M, double *C, int G, int J, int n,
+                                const GameStat *stats, cudaStream_t st)
+{
+    int64_t R = 1;
+    for (int s = 0; s < J - 1; ++s) R *= n;
+    if (J < 1 || n < 1 || R > kRfChainMax || G > 65535) return CHEB_EUNSUPPORTED;
+    if (G <= 0) return CHEB_OK;
+    static PerDevice attr;
+    cheb_status r = per_device_once(attr, [](int *) -> cheb_status {
+        CHEB_CUDA_TRY(cudaFuncSetAttribute(refit_df_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(dfl) * (kGameNMax * kGameNMax + 2 * kRfChainMax))));
+        return CHEB_OK;
+    }, nullptr);
+    if (r) return r;
+    const size_t smem = sizeof(dfl) * ((size_t)n * n + 2 * (size_t)R);
+    ProfScope prof("game_refit_df_chain J=" + std::to_string(J) + " n=" + std::to_string(n) + " G=" + std::to_string(G),
+                   st);
+    refit_df_chain_kernel<<<dim3((unsigned)n, (unsigned)G), kRfChainThreads, smem, st>>>(
+        reinterpret_cast<const dfl *>(Vdf), M, C, J, n, stats);
+    CHEB_CUDA_TRY(cudaGetLastError());
     return CHEB_OK;
 }
 

@@ -260,7 +260,7 @@ general_player_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         }
     }
     g.u_new[i * NP + j] = 0.5 * g.U_M * (ys + 1.0);
-    g.Vn_new[i * NP + j] = vs;
+    store_vn_new(g, i * NP + j, vs);
     const double dv = fabs(vs - g.Vn[i * NP + j]);
     atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(dv));
 }

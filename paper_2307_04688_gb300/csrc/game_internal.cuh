@@ -32,6 +32,8 @@ struct GameDev {
     void *bsplit;                 // pre-split coefficient operands, J x chunks
     // double-float path (game_df.cu)
     float *Cdf;                   // J x NP coefficient pairs (hi, lo)
+    float *Vdf;                   // J x NP pairs (hi, lo) of Vn_new: the double-float refit's input
+    double two_over_PM;           // 2 / P_M (next-state coordinates without a division)
     int polish_mode;              // mode a stalled split iteration continues in (0 FP64, 2 double-float)
     // general method (game_general.cu): dynamics coupled through gamma
     int general, n_u;             // general method on; control nodes per player
@@ -131,6 +133,20 @@ __device__ __forceinline__ double argmax_control(const double *w, int n, double 
     return best_u;
 }
 
+// Vn_new[idx] = V and, for groups that refit in double-float, its split
+// (hi = V rounded to FP32, lo = the rest rounded), the refit's input: formed
+// here once per value instead of by every refit CTA that reads it (the FP64
+// conversions run on GB300's slow FP64 pipe).
+__device__ __forceinline__ void store_vn_new(const GameDev &g, int idx, double V)
+{
+    g.Vn_new[idx] = V;
+    if (g.Vdf) {
+        const float hi = (float)V;
+        g.Vdf[2 * idx] = hi;
+        g.Vdf[2 * idx + 1] = (float)(V - (double)hi);
+    }
+}
+
 // Given the series w (player i's coordinate, node j), maximise, store the
 // new control and value, and fold |V_new - V_old| into the residual.
 __device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, int i, int j, const double *w)
@@ -146,7 +162,7 @@ __device__ __forceinline__ void player_finish(const GameDev &g, GameStat *st, in
     double V;
     const double us = argmax_control(w, g.n, xc, slope, hA, hG0, g.h, g.delta, g.U_M, ui, &V);
     g.u_new[i * NP + j] = us;
-    g.Vn_new[i * NP + j] = V;
+    store_vn_new(g, i * NP + j, V);
     const double d = fabs(V - g.Vn[i * NP + j]);
     atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
 }
@@ -166,11 +182,17 @@ cheb_status game_general_player(const GameDev *d_inst, GameStat *d_stat, int B, 
 cheb_status game_df_player(const GameDev *d_inst, GameStat *d_stat, int B, int J, int NP, cudaStream_t st);
 
 // ---- double-float refit of G = B J slabs (game_df.cu), for split-precision
-// solves: C = V with eq. (forcoef) applied along each of the J modes; slabs of
-// finished instances skipped when `stats` is given. n in {5, 9, 17, 33}.
+// solves: C = V with eq. (forcoef) applied along each of the J modes, from
+// the (hi, lo) pairs Vdf of the nodal values; slabs of finished instances
+// skipped when `stats` is given. game_refit_df: one launch per mode, n in
+// {5, 9, 17, 33}; game_refit_df_chain: all modes in one launch for small
+// groups (bit-identical coefficients; CHEB_EUNSUPPORTED, nothing launched,
+// when n^(J-1) > 4913 or G > 65535).
 bool game_refit_df_supported(int n);
-cheb_status game_refit_df(const double *V, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
+cheb_status game_refit_df(const float *Vdf, const double *M, double *C, double *tmp0, double *tmp1, int G, int J,
                           int n, int NP, const GameStat *stats, cudaStream_t st);
+cheb_status game_refit_df_chain(const float *Vdf, const double *M, double *C, int G, int J, int n,
+                                const GameStat *stats, cudaStream_t st);
 
 // ---- split-precision player update (game_tc.cu) ----
 bool tc_shape_supported(int J, int n);    // (J, n) with a split player update

@@ -703,7 +703,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                     V = bv;
                 }
                 g.u_new[i * NP + j] = us;
-                g.Vn_new[i * NP + j] = V;
+                store_vn_new(g, i * NP + j, V);
                 const double d = fabs(V - g.Vn[i * NP + j]);
                 atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
             }

@@ -140,9 +140,9 @@ def test_batch_instances_finishing_at_different_iterations(ctx, prec):
 @pytest.mark.parametrize("n,count", [(33, 8), (17, 24), (9, 81), (17, 1)])
 def test_split_refit_is_the_fp64_fit_of_the_nodal_values(ctx, n, count):
     """The coefficients a split-precision solve returns are the fit (eq. (forcoef) along every
-    mode, the oracle's FP64 DCT-I) of the nodal values it returns. Large groups (here 8 n = 33,
-    24 n = 17 or 81 n = 9 instances: over 300 tiles of 64 rows) refit in double-float on the
-    FP32 pipe, a single instance in FP64; both to 1e-13."""
+    mode, the oracle's FP64 DCT-I) of the nodal values it returns, to 1e-13. Split-precision
+    groups refit in double-float on the FP32 pipe: 24 n = 17 or 81 n = 9 instances one launch
+    per mode, 8 n = 33 instances and a single instance all modes in one launch."""
     rng = I.SplitMix64(5 + n + count)
     ps = [I.draw_game_params(rng, 3) for _ in range(count)]
     o = cb.game_opts(n, tol=0.0, max_iter=3, prec="bf16x6", polish_fp64=False)
@@ -451,3 +451,24 @@ def test_solves_are_bit_reproducible(ctx, prec, polish):
         assert r1[q].residual == r2[q].residual
         assert r1[q].iters <= its[q]
     ctx.device_status()
+
+
+def test_one_launch_refit_matches_the_per_mode_refit(ctx):
+    """The small-group refit (all modes in one launch per slab and last index) forms the same
+    compensated sums in the same order as the per-mode refit of large groups: an instance solved
+    alone and the same instance inside a 24-instance n = 17 group (per-mode refit) give
+    bit-identical coefficients, controls and nodal values (default tile shape in both)."""
+    rng = I.SplitMix64(321)
+    ps = [I.draw_game_params(rng, 3) for _ in range(24)]
+    o = cb.game_opts(17, tol=0.0, max_iter=4, prec="bf16x6", polish_fp64=False)
+    ctx.set_tuning(1)
+    try:
+        Vn_b = [torch.empty((3, 17 ** 3), dtype=torch.float64, device="cuda") for _ in range(24)]
+        Vb, ub, rb = cb.game_solve(ctx, ps, [o] * 24, Vn=Vn_b, raise_on_error=False)
+        Vn_1 = [torch.empty((3, 17 ** 3), dtype=torch.float64, device="cuda")]
+        V1, u1, r1 = cb.game_solve(ctx, ps[5], o, Vn=Vn_1, raise_on_error=False)
+    finally:
+        ctx.set_tuning(0)
+    assert rb[5].iters == r1[0].iters == 4
+    assert torch.equal(Vn_b[5], Vn_1[0]) and torch.equal(ub[5], u1[0])
+    assert torch.equal(Vb[5], V1[0])
