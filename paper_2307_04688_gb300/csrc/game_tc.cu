@@ -51,6 +51,10 @@ constexpr int kTile = 128;
 constexpr int kThreads = 256;
 constexpr int kProducer = kTile;    // issues the bulk copies and the MMAs (first thread of the upper half)
 constexpr int kPairs = 32;          // (instance, player) pairs interleaved in the work order
+// Step 3 inputs of a node, copied into shared memory at the start of its tile
+// (the copies complete during the column chunks): u_i, X_i, the old value and
+// the node's own Chebyshev node
+constexpr int kStep3 = 4;
 
 template <int FORM> struct GForm;
 template <> struct GForm<CHEB_BF16X3> {
@@ -112,7 +116,8 @@ template <int FORM, int JJ, int NN, int CH> struct Shape {
     static constexpr size_t SMEM = (size_t)F::SA * A_SPLIT + 2 * (size_t)CHUNK_BYTES +
                                    (size_t)NN * kTile * sizeof(float) +              // w
                                    (size_t)TAIL_FLOATS * sizeof(float) +
-                                   (size_t)STG * kTile * sizeof(float) + 128;
+                                   (size_t)STG * kTile * sizeof(float) +
+                                   (size_t)kStep3 * kTile * sizeof(double) + 128;     // Step 3 inputs
     // CTAs per SM that shared memory and TMEM allow, at most 2: the register
     // budget the kernel is compiled to (128 per thread at 2)
     static constexpr int MINB = (2 * (SMEM + 1024) <= 228 * 1024 && 2 * TMEM_ALLOC <= 512) ? 2 : 1;
@@ -331,7 +336,8 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
     float *w_s = reinterpret_cast<float *>(sB + 2 * S::CHUNK_BYTES);   // [NN][128]
     float *ct_s = w_s + NN * kTile;                                   // tail coefficients Ca (TAIL)
     float *tb_s = ct_s + S::TAIL_FLOATS;                              // [STG][128] staged T_{k_b}, T_{n-1}
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tb_s + S::STG * kTile);   // [0,1] B loads, [2,3] mma per accumulator
+    double *s3_s = reinterpret_cast<double *>(tb_s + S::STG * kTile);   // [kStep3][128] Step 3 inputs
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s3_s + kStep3 * kTile);   // [0,1] B loads, [2,3] mma per accumulator
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -510,6 +516,18 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         const uint8_t *bsrc = static_cast<const uint8_t *>(g.bsplit) + (size_t)i * S::PLAYER_BYTES;
         const int j = t * kTile + row;
         const bool valid = j < NP;
+        // Step 3's global inputs of this thread's node, in flight while the
+        // column chunks run (the lower half reads them after the chunks)
+        if (half == 0) {
+            if (valid) {
+                const int ki = (j / mode_stride<JJ, NN>(i)) % NN;
+                cp_async8(&s3_s[0 * kTile + tid], g.u + i * NP + j);
+                cp_async8(&s3_s[1 * kTile + tid], g.X + i * NP + j);
+                cp_async8(&s3_s[2 * kTile + tid], g.Vn + i * NP + j);
+                cp_async8(&s3_s[3 * kTile + tid], g.nodes + ki);
+            }
+            cp_async_commit();
+        }
         // the epilogue factors of this thread's row, from the stage: J = 3
         // T_{k_b}(x_b(j)); J = 4 T_{k_b}(x_b(j)) and T_{k_c}(x_c(j))
         constexpr int NTB = JJ == 3 ? S::NBP : 1;
@@ -634,12 +652,13 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
 #pragma unroll
                 for (int k = 0; k < NN; ++k) w[k] = w_s[k * kTile + tid];
                 // the node's own coordinate (row-major multi-index, last player
-                // fastest) and the per-player constants formed on the host
-                const int ki = (j / mode_stride<JJ, NN>(i)) % NN;
-                const double pbi = 0.5 * g.P_M * (g.nodes[ki] + 1.0);
-                const double ui = g.u[i * NP + j];
+                // fastest; its Chebyshev node came with the other inputs) and
+                // the per-player constants formed on the host
+                cp_async_wait_all();
+                const double pbi = 0.5 * g.P_M * (s3_s[3 * kTile + tid] + 1.0);
+                const double ui = s3_s[0 * kTile + tid];
                 const double slope = g.slope[i];
-                const double xc = g.X[i * NP + j] - slope * ui;
+                const double xc = s3_s[1 * kTile + tid] - slope * ui;
                 const double hA = g.hA[i];
                 const double hG0 = g.hphi2[i] * pbi * pbi;
                 const float U_M = (float)g.U_M;
@@ -685,6 +704,44 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                     s += (double)acc.hi + (double)acc.lo;
                     return hA * uu - 0.5 * g.h * uu * uu + hG0 + g.delta * s;
                 };
+                // the same at three controls, the three recurrences interleaved
+                // (independent chains: one evaluation's latency for all three)
+                auto value64x3 = [&](const double (&uu)[3], double (&out)[3]) {
+                    ff xf[3], x2[3], t0[3], t1[3], acc[3];
+                    double s[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        xf[c] = ff_from_double(xc + slope * uu[c]);
+                        x2[c] = {2.0f * xf[c].hi, 2.0f * xf[c].lo};
+                        t0[c] = {1.0f, 0.0f};
+                        t1[c] = xf[c];
+                        acc[c] = {0.0f, 0.0f};
+                        s[c] = (double)w[0] + (double)w[1] * ((double)xf[c].hi + (double)xf[c].lo);
+                    }
+#pragma unroll
+                    for (int m = 2; m < NN; ++m) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const ff t2 = ff_cheb_step(x2[c], t1[c], t0[c]);
+                            const float p = w[m] * t2.hi;
+                            float e = fmaf(w[m], t2.hi, -p);
+                            e = fmaf(w[m], t2.lo, e);
+                            const float sh = acc[c].hi + p;
+                            const float bb = sh - acc[c].hi;
+                            const float er = (acc[c].hi - (sh - bb)) + (p - bb);
+                            float lo = acc[c].lo + e + er;
+                            acc[c].hi = sh + lo;
+                            acc[c].lo = lo - (acc[c].hi - sh);
+                            t0[c] = t1[c];
+                            t1[c] = t2;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        s[c] += (double)acc[c].hi + (double)acc[c].lo;
+                        out[c] = hA * uu[c] - 0.5 * g.h * uu[c] * uu[c] + hG0 + g.delta * s[c];
+                    }
+                };
                 double us = (double)u;
                 double V;
                 if (u > 0.0f && u < U_M && W2 < 0.0f) {
@@ -694,17 +751,18 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
                     // at a bound or not concave: the bounds and the Newton point
                     // compete in FP64 (differences of W near a bound are far below
                     // FP32 resolution), ties to the smaller control
-                    double bu = 0.0, bv = value64(0.0);
-                    const double vn = value64(us);
-                    if (vn > bv) { bv = vn; bu = us; }
-                    const double vm = value64(g.U_M);
-                    if (vm > bv) { bv = vm; bu = g.U_M; }
+                    const double cu[3] = {0.0, us, g.U_M};
+                    double cv[3];
+                    value64x3(cu, cv);
+                    double bu = 0.0, bv = cv[0];
+                    if (cv[1] > bv) { bv = cv[1]; bu = us; }
+                    if (cv[2] > bv) { bv = cv[2]; bu = g.U_M; }
                     us = bu;
                     V = bv;
                 }
                 g.u_new[i * NP + j] = us;
                 store_vn_new(g, i * NP + j, V);
-                const double d = fabs(V - g.Vn[i * NP + j]);
+                const double d = fabs(V - s3_s[2 * kTile + tid]);
                 atomicMax(&st->res_bits, (unsigned long long)__double_as_longlong(d));
             }
         } else if (next < items) {
@@ -716,6 +774,7 @@ game_player_tc_kernel(const GameDev *__restrict__ insts, GameStat *__restrict__ 
         item = next;
     }
     // drain copies and MMAs in flight (abort path), free TMEM
+    cp_async_wait_all();
     if (tid == kProducer) {
         for (int s2 = 0; s2 < 2; ++s2)
             if (pending & (1u << s2)) mbar_wait_bounded(&bars[s2], (ld_phase >> s2) & 1u, err);

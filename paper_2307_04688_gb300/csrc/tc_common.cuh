@@ -86,6 +86,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// ---- per-thread asynchronous copy global -> shared (8 bytes) -----------------
+// Completes for the issuing thread at its cp_async_wait_all(); both addresses
+// 8-byte aligned.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ---- bulk copy shared -> global (TMA engine, non-tensor form) ---------------
 // dst and src 16-byte aligned, bytes a multiple of 16; tracked in bulk groups
 // of the issuing thread.
