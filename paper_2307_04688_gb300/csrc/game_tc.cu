@@ -28,9 +28,8 @@
 //    registers) and writes w_j[k_i] to shared memory;
 //  - after the last chunk, one thread per node of the lower 128 maximises
 //    over its control (Newton in FP32 from the previous control, the value at
-//    the maximiser in double-float and FP64; its inputs were copied into shared
-//    memory by per-thread async copies at the start of the tile) and writes the
-//    new control, value and the FP64 residual, while the upper 128 threads run the next tile's
+//    the maximiser in double-float and FP64) and writes the new control, value
+//    and the FP64 residual, while the upper 128 threads run the next tile's
 //    prologue (A operand, T_{k_b} rows staged in shared memory, first B
 //    copies, first MMA); the first thread of the upper half issues every bulk
 //    copy and MMA.
